@@ -1,0 +1,206 @@
+"""Plain CPU oracle for rectangular binary morphology and run-length coding.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  The product library never calls it, and the two share no code.
+
+The arithmetic lives in ``morph_oracle.c`` (plain loops on unpacked bytes, see
+its header for the definitions and the boundary reading).  This module only
+compiles it with gcc, loads it with ctypes and marshals numpy arrays.
+
+Conventions (all arrays are numpy):
+  * a bitmap is ``uint8[H, W]`` with values 0/1, row 0 first;
+  * an RLE image is ``(row_ptr int32[H+1], runs uint16[N, 2])`` with runs
+    ``[start, end)`` per row, ascending and separated by gaps (the paper's
+    section "Run Length Image Coding", half-open reading).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "morph_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``morph_oracle.c`` into ``liboracle.so`` (gcc, OpenMP)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + ".%d.tmp" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-fvisibility=hidden",
+           "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            u8p = ctypes.POINTER(ctypes.c_uint8)
+            i32p = ctypes.POINTER(ctypes.c_int32)
+            u16p = ctypes.POINTER(ctypes.c_uint16)
+            ci = ctypes.c_int
+            for name in ("oracle_erode_rect", "oracle_dilate_rect"):
+                f = getattr(lib, name)
+                f.argtypes = [u8p, u8p, ci, ci, ci, ci, ci, ci, ci]
+                f.restype = None
+            for name in ("oracle_erode_rect_sep", "oracle_dilate_rect_sep"):
+                f = getattr(lib, name)
+                f.argtypes = [u8p, u8p, ci, ci, ci, ci, ci, ci, ci]
+                f.restype = ci
+            lib.oracle_rect_batch.argtypes = [u8p, u8p, ctypes.c_int64, ci, ci, ci, ci, ci, ci, ci]
+            lib.oracle_rect_batch.restype = ci
+            lib.oracle_rle_count.argtypes = [i32p, u8p, ci, ci]
+            lib.oracle_rle_count.restype = ctypes.c_int64
+            lib.oracle_rle_encode.argtypes = [i32p, u16p, u8p, ci, ci]
+            lib.oracle_rle_encode.restype = None
+            lib.oracle_rle_decode.argtypes = [u8p, i32p, u16p, ci, ci]
+            lib.oracle_rle_decode.restype = ci
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _as_img(img) -> np.ndarray:
+    a = np.ascontiguousarray(img, dtype=np.uint8)
+    if a.ndim != 2:
+        raise ValueError("bitmap must be 2D uint8")
+    if a.size and a.max() > 1:
+        raise ValueError("bitmap values must be 0/1")
+    return a
+
+
+def _check_se(sw, sh, ox, oy):
+    if sw < 1 or sh < 1 or not (0 <= ox < sw) or not (0 <= oy < sh):
+        raise ValueError("bad structuring element %dx%d origin (%d,%d)" % (sw, sh, ox, oy))
+
+
+def centre(sw: int, sh: int):
+    """Default origin of a sw x sh rectangle: (floor(sw/2), floor(sh/2))."""
+    return sw // 2, sh // 2
+
+
+# ------------------------------------------------------------ rectangle ops
+
+def erode(img, sw, sh, ox=None, oy=None, mode="brute", threads=1) -> np.ndarray:
+    """Clipped-window erosion by a sw x sh rectangle with origin (ox, oy)."""
+    return _rect(img, sw, sh, ox, oy, mode, threads, dilate=False)
+
+
+def dilate(img, sw, sh, ox=None, oy=None, mode="brute", threads=1) -> np.ndarray:
+    """Clipped-window dilation (reflected rectangle) with origin (ox, oy)."""
+    return _rect(img, sw, sh, ox, oy, mode, threads, dilate=True)
+
+
+def opening(img, sw, sh, ox=None, oy=None, mode="brute", threads=1) -> np.ndarray:
+    """Opening = dilation of the erosion, same rectangle and origin."""
+    e = erode(img, sw, sh, ox, oy, mode, threads)
+    return dilate(e, sw, sh, ox, oy, mode, threads)
+
+
+def closing(img, sw, sh, ox=None, oy=None, mode="brute", threads=1) -> np.ndarray:
+    """Closing = erosion of the dilation, same rectangle and origin."""
+    d = dilate(img, sw, sh, ox, oy, mode, threads)
+    return erode(d, sw, sh, ox, oy, mode, threads)
+
+
+OPS = {"erode": erode, "dilate": dilate, "open": opening, "close": closing}
+
+
+def apply(op: str, img, sw, sh, ox=None, oy=None, mode="brute", threads=1) -> np.ndarray:
+    return OPS[op](img, sw, sh, ox, oy, mode, threads)
+
+
+def _rect(img, sw, sh, ox, oy, mode, threads, dilate):
+    if ox is None or oy is None:
+        cx, cy = centre(sw, sh)
+        ox = cx if ox is None else ox
+        oy = cy if oy is None else oy
+    _check_se(sw, sh, ox, oy)
+    a = _as_img(img)
+    H, W = a.shape
+    out = np.empty_like(a)
+    if a.size == 0:
+        return out
+    lib = _load()
+    if mode == "brute":
+        f = lib.oracle_dilate_rect if dilate else lib.oracle_erode_rect
+        f(_ptr(out, ctypes.c_uint8), _ptr(a, ctypes.c_uint8), W, H, sw, sh, ox, oy, threads)
+    elif mode == "separable":
+        f = lib.oracle_dilate_rect_sep if dilate else lib.oracle_erode_rect_sep
+        if f(_ptr(out, ctypes.c_uint8), _ptr(a, ctypes.c_uint8), W, H, sw, sh, ox, oy, threads):
+            raise MemoryError("oracle separable mode: allocation failed")
+    else:
+        raise ValueError("mode must be 'brute' or 'separable'")
+    return out
+
+
+def rect_batch(imgs: np.ndarray, sw, sh, ox, oy, op: str) -> np.ndarray:
+    """Apply one op to n images ``uint8[n, H, W]`` (brute force)."""
+    _check_se(sw, sh, ox, oy)
+    a = np.ascontiguousarray(imgs, dtype=np.uint8)
+    n, H, W = a.shape
+    out = np.empty_like(a)
+    code = {"erode": 0, "dilate": 1, "open": 2, "close": 3}[op]
+    if _load().oracle_rect_batch(_ptr(out, ctypes.c_uint8), _ptr(a, ctypes.c_uint8), n, W, H,
+                                 sw, sh, ox, oy, code):
+        raise MemoryError("oracle batch: allocation failed")
+    return out
+
+
+# ----------------------------------------------------------------- RLE
+
+def rle_encode(img):
+    """Canonical runs of each row -> (row_ptr int32[H+1], runs uint16[N, 2])."""
+    a = _as_img(img)
+    H, W = a.shape
+    if W > 65535:
+        raise ValueError("RLE rows are limited to 65535 pixels (16-bit run ends)")
+    lib = _load()
+    n = int(lib.oracle_rle_count(None, _ptr(a, ctypes.c_uint8), W, H)) if a.size else 0
+    row_ptr = np.zeros(H + 1, dtype=np.int32)
+    runs = np.zeros((n, 2), dtype=np.uint16)
+    if a.size:
+        lib.oracle_rle_encode(_ptr(row_ptr, ctypes.c_int32), _ptr(runs, ctypes.c_uint16),
+                              _ptr(a, ctypes.c_uint8), W, H)
+    return row_ptr, runs
+
+
+def rle_decode(row_ptr, runs, W: int, H: int) -> np.ndarray:
+    """Paint the runs of each row into a 0/1 bitmap.  Raises on a run list
+    that is not canonical (empty, out of range, touching or unsorted)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    rn = np.ascontiguousarray(runs, dtype=np.uint16).reshape(-1, 2)
+    if rp.shape != (H + 1,) or rp[0] != 0 or rp[-1] != rn.shape[0] or np.any(np.diff(rp) < 0):
+        raise ValueError("row_ptr is not a valid prefix array")
+    out = np.empty((H, W), dtype=np.uint8)
+    if out.size == 0:
+        return out
+    if rn.shape[0] == 0:
+        rn = np.zeros((1, 2), dtype=np.uint16)
+    if _load().oracle_rle_decode(_ptr(out, ctypes.c_uint8), _ptr(rp, ctypes.c_int32),
+                                 _ptr(rn, ctypes.c_uint16), W, H):
+        raise ValueError("run list is not canonical")
+    return out
+
+
+def rle_apply(op: str, row_ptr, runs, W, H, sw, sh, ox=None, oy=None, mode="brute", threads=1):
+    """Morphology on an RLE image, by its plain definition: decode, apply the
+    byte-image op, encode the result."""
+    img = rle_decode(row_ptr, runs, W, H)
+    return rle_encode(apply(op, img, sw, sh, ox, oy, mode, threads))

@@ -1,0 +1,258 @@
+/*
+ * Plain CPU oracle for rectangular binary morphology and run-length coding.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call this code:
+ * only tests/, the smoke check in __graft_entry__ and the cpu_baseline leg of
+ * bench.py load it.  It shares no source with the CUDA library.
+ *
+ * Images are unpacked: one byte per pixel, value 0 or 1, row-major, row 0
+ * first, W bytes per row, no padding.  Pixel (x, y) is in[y * W + x].
+ *
+ * Definitions (the paper's set semantics, written out literally):
+ *
+ *   erosion  (paper, section "Within-Line Morphological Operations", 1D
+ *             erosion; section "2D Morphological Operators for Rectangular
+ *             Masks", brute force used "for reference and verification"):
+ *       E(x,y) = min { I(x+i-ox, y+j-oy) : 0<=i<sw, 0<=j<sh, inside image }
+ *   dilation (the reflected structuring element, Minkowski addition):
+ *       D(x,y) = max { I(x-i+ox, y-j+oy) : 0<=i<sw, 0<=j<sh, inside image }
+ *   opening  = D(E(I)), closing = E(D(I))  (section "Within-Line ...": opening
+ *             and closing are not separable and are built from erosions and
+ *             dilations).
+ *
+ * Boundary reading: positions outside the image are simply left out of the
+ * min / max ("clipped window").  Erosion therefore behaves as if the outside
+ * were 1 and dilation as if it were 0.  The paper's text is not consistent on
+ * this point (its 1D erosion shrinks runs at the border, its complement closes
+ * the last gap at maxint); the clipped window is the reading under which
+ * duality, separability, idempotence and (anti-)extensivity all hold exactly.
+ *
+ * Run-length coding (section "Run Length Image Coding"): each row is the
+ * ascending list of its maximal runs of 1-pixels, each run stored as two
+ * 16-bit numbers (start, end) with end exclusive ("half-open" reading of the
+ * paper's [s, e]; its complement routine uses half-open intervals).
+ *
+ * Two evaluation modes for the rectangle operations:
+ *   brute force  — the definition above, pixel by pixel;
+ *   separable    — a 1D pass along rows then a 1D pass along columns, the
+ *                  decomposition erode2d = erode1d, transpose, erode1d given
+ *                  in section "Morphological Operations".  Each 1D pass is
+ *                  still the plain clipped min / max over its window.
+ * The tests check the two modes against each other.
+ *
+ * Optional threading: `nthreads` > 1 splits the independent output rows over
+ * OpenMP threads; it does not change any result.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define EXPORT __attribute__((visibility("default")))
+
+static void set_threads(int nthreads) {
+#ifdef _OPENMP
+    omp_set_num_threads(nthreads > 0 ? nthreads : 1);
+#else
+    (void)nthreads;
+#endif
+}
+
+/* ---------------------------------------------------------------- brute */
+
+/* E(x,y) = min over the clipped window.  Early exit on the first 0 does not
+ * change the minimum of 0/1 values. */
+EXPORT void oracle_erode_rect(uint8_t *out, const uint8_t *in, int W, int H,
+                              int sw, int sh, int ox, int oy, int nthreads) {
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 8) if (nthreads > 1)
+    for (int y = 0; y < H; y++) {
+        for (int x = 0; x < W; x++) {
+            uint8_t v = 1;
+            for (int j = 0; j < sh && v; j++) {
+                int yy = y + j - oy;
+                if (yy < 0 || yy >= H) continue;
+                for (int i = 0; i < sw; i++) {
+                    int xx = x + i - ox;
+                    if (xx < 0 || xx >= W) continue;
+                    if (in[(size_t)yy * W + xx] == 0) { v = 0; break; }
+                }
+            }
+            out[(size_t)y * W + x] = v;
+        }
+    }
+}
+
+/* D(x,y) = max over the clipped, reflected window. */
+EXPORT void oracle_dilate_rect(uint8_t *out, const uint8_t *in, int W, int H,
+                               int sw, int sh, int ox, int oy, int nthreads) {
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 8) if (nthreads > 1)
+    for (int y = 0; y < H; y++) {
+        for (int x = 0; x < W; x++) {
+            uint8_t v = 0;
+            for (int j = 0; j < sh && !v; j++) {
+                int yy = y - j + oy;
+                if (yy < 0 || yy >= H) continue;
+                for (int i = 0; i < sw; i++) {
+                    int xx = x - i + ox;
+                    if (xx < 0 || xx >= W) continue;
+                    if (in[(size_t)yy * W + xx] != 0) { v = 1; break; }
+                }
+            }
+            out[(size_t)y * W + x] = v;
+        }
+    }
+}
+
+/* ----------------------------------------------------------- separable */
+
+/* 1D pass along rows: window of sw pixels, origin ox; erode = min, dilate =
+ * max over the reflected window.  Clipped at the row ends. */
+static void pass_rows(uint8_t *out, const uint8_t *in, int W, int H, int sw,
+                      int ox, int dilate, int nthreads) {
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 8) if (nthreads > 1)
+    for (int y = 0; y < H; y++) {
+        const uint8_t *r = in + (size_t)y * W;
+        uint8_t *o = out + (size_t)y * W;
+        for (int x = 0; x < W; x++) {
+            uint8_t v = dilate ? 0 : 1;
+            for (int i = 0; i < sw; i++) {
+                int xx = dilate ? x - i + ox : x + i - ox;
+                if (xx < 0 || xx >= W) continue;
+                if (dilate) { if (r[xx]) { v = 1; break; } }
+                else        { if (!r[xx]) { v = 0; break; } }
+            }
+            o[x] = v;
+        }
+    }
+}
+
+/* 1D pass along columns: window of sh rows, origin oy. */
+static void pass_cols(uint8_t *out, const uint8_t *in, int W, int H, int sh,
+                      int oy, int dilate, int nthreads) {
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 8) if (nthreads > 1)
+    for (int y = 0; y < H; y++) {
+        uint8_t *o = out + (size_t)y * W;
+        for (int x = 0; x < W; x++) {
+            uint8_t v = dilate ? 0 : 1;
+            for (int j = 0; j < sh; j++) {
+                int yy = dilate ? y - j + oy : y + j - oy;
+                if (yy < 0 || yy >= H) continue;
+                uint8_t p = in[(size_t)yy * W + x];
+                if (dilate) { if (p) { v = 1; break; } }
+                else        { if (!p) { v = 0; break; } }
+            }
+            o[x] = v;
+        }
+    }
+}
+
+static int rect_sep(uint8_t *out, const uint8_t *in, int W, int H, int sw,
+                    int sh, int ox, int oy, int dilate, int nthreads) {
+    uint8_t *tmp = (uint8_t *)malloc((size_t)W * H);
+    if (!tmp) return -1;
+    pass_rows(tmp, in, W, H, sw, ox, dilate, nthreads);
+    pass_cols(out, tmp, W, H, sh, oy, dilate, nthreads);
+    free(tmp);
+    return 0;
+}
+
+EXPORT int oracle_erode_rect_sep(uint8_t *out, const uint8_t *in, int W, int H,
+                                 int sw, int sh, int ox, int oy, int nthreads) {
+    return rect_sep(out, in, W, H, sw, sh, ox, oy, 0, nthreads);
+}
+
+EXPORT int oracle_dilate_rect_sep(uint8_t *out, const uint8_t *in, int W, int H,
+                                  int sw, int sh, int ox, int oy, int nthreads) {
+    return rect_sep(out, in, W, H, sw, sh, ox, oy, 1, nthreads);
+}
+
+/* ------------------------------------------------------------- batches */
+
+/* n independent images of W x H stored back to back (used by the exhaustive
+ * tiny-image checks).  op: 0 erode, 1 dilate, 2 open, 3 close. */
+EXPORT int oracle_rect_batch(uint8_t *out, const uint8_t *in, int64_t n, int W,
+                             int H, int sw, int sh, int ox, int oy, int op) {
+    size_t px = (size_t)W * H;
+    uint8_t *tmp = (uint8_t *)malloc(px);
+    if (!tmp) return -1;
+    for (int64_t k = 0; k < n; k++) {
+        const uint8_t *a = in + (size_t)k * px;
+        uint8_t *b = out + (size_t)k * px;
+        switch (op) {
+        case 0: oracle_erode_rect(b, a, W, H, sw, sh, ox, oy, 1); break;
+        case 1: oracle_dilate_rect(b, a, W, H, sw, sh, ox, oy, 1); break;
+        case 2:
+            oracle_erode_rect(tmp, a, W, H, sw, sh, ox, oy, 1);
+            oracle_dilate_rect(b, tmp, W, H, sw, sh, ox, oy, 1);
+            break;
+        default:
+            oracle_dilate_rect(tmp, a, W, H, sw, sh, ox, oy, 1);
+            oracle_erode_rect(b, tmp, W, H, sw, sh, ox, oy, 1);
+            break;
+        }
+    }
+    free(tmp);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ RLE */
+
+/* Number of maximal runs of 1s in each row; returns the total. */
+EXPORT int64_t oracle_rle_count(int32_t *row_counts, const uint8_t *in, int W,
+                                int H) {
+    int64_t total = 0;
+    for (int y = 0; y < H; y++) {
+        const uint8_t *r = in + (size_t)y * W;
+        int32_t c = 0;
+        for (int x = 0; x < W; x++)
+            if (r[x] && (x == 0 || !r[x - 1])) c++;
+        if (row_counts) row_counts[y] = c;
+        total += c;
+    }
+    return total;
+}
+
+/* Canonical runs of each row: row_ptr[H+1] (prefix of counts) and runs as
+ * uint16 pairs (start, end), end exclusive, ascending, separated by gaps. */
+EXPORT void oracle_rle_encode(int32_t *row_ptr, uint16_t *runs,
+                              const uint8_t *in, int W, int H) {
+    int64_t k = 0;
+    row_ptr[0] = 0;
+    for (int y = 0; y < H; y++) {
+        const uint8_t *r = in + (size_t)y * W;
+        int x = 0;
+        while (x < W) {
+            if (!r[x]) { x++; continue; }
+            int s = x;
+            while (x < W && r[x]) x++;
+            runs[2 * k] = (uint16_t)s;
+            runs[2 * k + 1] = (uint16_t)x;
+            k++;
+        }
+        row_ptr[y + 1] = (int32_t)k;
+    }
+}
+
+/* Paint every run [start, end) of every row; everything else is 0.
+ * Returns 0, or -1 if a run is empty, out of range, or not ascending. */
+EXPORT int oracle_rle_decode(uint8_t *out, const int32_t *row_ptr,
+                             const uint16_t *runs, int W, int H) {
+    memset(out, 0, (size_t)W * H);
+    for (int y = 0; y < H; y++) {
+        uint8_t *r = out + (size_t)y * W;
+        int prev_end = -1;
+        for (int32_t k = row_ptr[y]; k < row_ptr[y + 1]; k++) {
+            int s = runs[2 * k], e = runs[2 * k + 1];
+            if (s >= e || e > W || s <= prev_end) return -1;
+            for (int x = s; x < e; x++) r[x] = 1;
+            prev_end = e;
+        }
+    }
+    return 0;
+}

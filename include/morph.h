@@ -1,0 +1,188 @@
+/*
+ * morph.h — C ABI of the GB300 binary / run-length morphology library.
+ *
+ * Binary erosion, dilation, opening and closing with rectangular structuring
+ * elements (SEs) on packed bitmaps and on row-wise run-length (RLE) images,
+ * and the conversions between the two formats (Breuel, "Efficient Binary and
+ * Run Length Morphology and its Application to Document Image Processing").
+ *
+ * Every buffer named here is DEVICE memory owned by the caller; the library
+ * never allocates device memory.  Scratch space, where an operation needs it,
+ * is passed in as `workspace` (size from morph_workspace_size).  All work is
+ * enqueued asynchronously on the caller's CUDA stream (`stream` is a
+ * cudaStream_t; NULL = the legacy default stream).  The returned status covers
+ * argument checks and the launches; conditions that only the device can see
+ * (an RLE output larger than its capacity, a bounded wait that gave up) are
+ * latched in a device-side status word and reported by morph_sync_status().
+ *
+ * Pixel conventions (identical for every entry point):
+ *   - pixel (x, y): x = column 0..W-1, y = row 0..H-1, row 0 first in memory;
+ *   - 1 = ink (foreground), 0 = background;
+ *   - packed rows are little-endian bit strings: pixel x of a row is bit
+ *     (x mod B) of word (x div B), B = 32 (MORPH_PACKED32) or 64
+ *     (MORPH_PACKED64).  Bits at x >= W ("padding bits") are ignored on input
+ *     and written as 0 on output;
+ *   - an RLE row is the ascending list of its maximal runs of 1s, each run a
+ *     pair of uint16 (start, end) with end EXCLUSIVE, separated by at least one
+ *     0-pixel (section "Run Length Image Coding": runs as pairs of 16-bit
+ *     integers, so W <= 65535 for RLE images).  runs[2k], runs[2k+1] are the
+ *     start and end of run k; the runs of row y are k in
+ *     [row_ptr[y], row_ptr[y+1]).
+ *
+ * Structuring element: a rectangle of se_w x se_h pixels (width x height) with
+ * origin (origin_x, origin_y), 0 <= origin_x < se_w, 0 <= origin_y < se_h; the
+ * centre of an odd rectangle is (se_w/2, se_h/2).  Definitions (clipped
+ * window: pixels outside the image are left out of the min / max, so erosion
+ * sees the outside as 1 and dilation as 0):
+ *   erode : E(x,y) = min { I(x+i-ox, y+j-oy) : 0<=i<se_w, 0<=j<se_h, in image }
+ *   dilate: D(x,y) = max { I(x-i+ox, y-j+oy) : 0<=i<se_w, 0<=j<se_h, in image }
+ *   open  = dilate(erode(I)), close = erode(dilate(I)), same SE and origin
+ * (sections "Within-Line Morphological Operations" — 1D erosion and dilation,
+ * opening and closing built from them — and "2D Morphological Operators for
+ * Rectangular Masks" — separable composition of within-line and between-line
+ * operations).
+ */
+#ifndef MORPH_H
+#define MORPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MORPH_ABI_VERSION 1
+
+#if defined(__GNUC__)
+#define MORPH_API __attribute__((visibility("default")))
+#else
+#define MORPH_API
+#endif
+
+typedef enum morph_status {
+    MORPH_OK = 0,
+    MORPH_EINVAL = 1,     /* bad argument (sizes, formats, SE, aliasing, NULL) */
+    MORPH_ECAPACITY = 2,  /* an RLE output needed more runs than capacity_runs */
+    MORPH_ENOMEM = 3,     /* workspace smaller than morph_workspace_size() */
+    MORPH_ECUDA = 4,      /* a CUDA launch or copy failed (see morph_last_error) */
+    MORPH_ETIMEOUT = 5    /* a bounded device-side wait gave up */
+} morph_status;
+
+typedef enum morph_format {
+    MORPH_PACKED32 = 0,   /* rows of uint32 words */
+    MORPH_PACKED64 = 1,   /* rows of uint64 words */
+    MORPH_RLE = 2         /* CSR of uint16 (start, end) runs */
+} morph_format;
+
+typedef enum morph_op {
+    MORPH_ERODE = 0,
+    MORPH_DILATE = 1,
+    MORPH_OPEN = 2,
+    MORPH_CLOSE = 3
+} morph_op;
+
+/* Descriptor of one image.  Only the fields of its format are read.
+ *   packed: words (device, aligned to the word size), stride_words >=
+ *           ceil(width / B) words of B bits between consecutive rows.
+ *   RLE   : row_ptr (device int32[height+1], row_ptr[0] = 0), runs (device
+ *           uint16[2*capacity_runs]), n_runs (device int64, may be NULL for
+ *           inputs).  As an OUTPUT, the producer writes row_ptr, the runs and
+ *           *n_runs = total runs needed; if that exceeds capacity_runs the runs
+ *           are not written and MORPH_ECAPACITY is latched (row_ptr and *n_runs
+ *           still tell the caller how much room to provide).
+ * The descriptor itself lives in host memory and is only read during the
+ * call; the buffers it points to must stay valid until the stream work ends. */
+typedef struct morph_image {
+    int32_t fmt;            /* morph_format */
+    int32_t width;          /* W >= 1 (<= 65535 for RLE) */
+    int32_t height;         /* H >= 1 */
+    int32_t reserved;       /* must be 0 */
+    void *words;            /* packed: row 0 */
+    int64_t stride_words;   /* packed: words per row, in the format's words */
+    int32_t *row_ptr;       /* RLE: int32[H+1] */
+    uint16_t *runs;         /* RLE: uint16[2*capacity_runs] */
+    int64_t capacity_runs;  /* RLE: room in runs, in runs */
+    int64_t *n_runs;        /* RLE output: int64 written on the device */
+} morph_image;
+
+/* ------------------------------------------------------------------ ops --
+ * Rectangular morphology.  dst and src have the same width and height and
+ * the same family of format: both packed (PACKED32 / PACKED64, may differ) or
+ * both RLE.  dst may not overlap src (use a second buffer; the paper's
+ * in-place convention is not kept because tiles of one launch read rows that
+ * other tiles write).
+ *
+ * Packed path: one launch of the fused tile kernel (within-line pass on
+ * packed words, between-line pass as bit-sliced run counters down word
+ * columns; opening / closing fuse both operations in the same launch).
+ * Workspace: none (workspace may be NULL, workspace_bytes 0), except for a
+ * rectangle reaching more than 128 pixels left or right of its origin
+ * (after clipping to the image), which runs as a chain of launches through
+ * scratch images in the workspace.
+ * RLE path: the row pass shrinks or grows every run and merges the grown
+ * ones (section "Within-Line Morphological Operations"); the between-line
+ * pass intersects (erode) or unites (dilate) se_h neighbouring rows, then a
+ * count / prefix-sum / write sequence produces the CSR output.  Workspace:
+ * morph_workspace_size() bytes, 256-byte aligned.
+ *
+ * Errors: MORPH_EINVAL for a bad SE, size, format, alias or NULL pointer;
+ * MORPH_ENOMEM if workspace_bytes is too small; MORPH_ECUDA if a launch
+ * failed.  MORPH_ECAPACITY for an RLE dst is latched on the device.
+ */
+MORPH_API morph_status morph_erode_rect(const morph_image *dst, const morph_image *src, int se_w,
+                              int se_h, int origin_x, int origin_y, void *workspace,
+                              size_t workspace_bytes, void *stream);
+MORPH_API morph_status morph_dilate_rect(const morph_image *dst, const morph_image *src, int se_w,
+                               int se_h, int origin_x, int origin_y, void *workspace,
+                               size_t workspace_bytes, void *stream);
+MORPH_API morph_status morph_open_rect(const morph_image *dst, const morph_image *src, int se_w,
+                             int se_h, int origin_x, int origin_y, void *workspace,
+                             size_t workspace_bytes, void *stream);
+MORPH_API morph_status morph_close_rect(const morph_image *dst, const morph_image *src, int se_w,
+                              int se_h, int origin_x, int origin_y, void *workspace,
+                              size_t workspace_bytes, void *stream);
+
+/* Same four operations selected by `op` (morph_op). */
+MORPH_API morph_status morph_rect(int op, const morph_image *dst, const morph_image *src, int se_w,
+                        int se_h, int origin_x, int origin_y, void *workspace,
+                        size_t workspace_bytes, void *stream);
+
+/* Bytes of workspace that morph_rect(op, dst, src, se_w, se_h, origin_x,
+ * origin_y, ...) needs: 0 for the packed path unless the rectangle is wider
+ * than one launch reaches; for RLE it depends on the op and image size only.
+ * Returns 0 for invalid arguments (the op call then reports them). */
+MORPH_API size_t morph_workspace_size(int op, const morph_image *dst, const morph_image *src,
+                                      int se_w, int se_h, int origin_x, int origin_y);
+
+/* ------------------------------------------------------------ conversion --
+ * Section "Conversion Between Image Formats".
+ * rle_from_bitmap: packed src -> RLE dst (canonical runs of every row).  A
+ * row's transitions are found with shifts and XOR, counted with popcount,
+ * their output positions come from a prefix sum over rows.  Workspace:
+ * morph_convert_workspace_size(height) bytes.
+ * rle_to_bitmap: RLE src -> packed dst; padding bits written 0.  No workspace.
+ * The src RLE must be canonical (as every producer here writes it); a
+ * non-canonical list gives an unspecified bitmap but no out-of-bounds access.
+ */
+MORPH_API size_t morph_convert_workspace_size(int height);
+MORPH_API morph_status rle_from_bitmap(const morph_image *dst_rle, const morph_image *src_packed,
+                             void *workspace, size_t workspace_bytes, void *stream);
+MORPH_API morph_status rle_to_bitmap(const morph_image *dst_packed, const morph_image *src_rle,
+                           void *stream);
+
+/* ---------------------------------------------------------------- status -- */
+/* Wait for `stream`, then return (and clear) the first device-side condition
+ * latched since the last call (MORPH_ECAPACITY, MORPH_ETIMEOUT), else the
+ * stream's CUDA error as MORPH_ECUDA, else MORPH_OK. */
+MORPH_API morph_status morph_sync_status(void *stream);
+/* Message for the last non-OK status returned on this host thread. */
+MORPH_API const char *morph_last_error(void);
+MORPH_API const char *morph_status_string(int status);
+MORPH_API int morph_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MORPH_H */

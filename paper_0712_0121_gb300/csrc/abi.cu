@@ -1,0 +1,437 @@
+// C ABI entry points of libmorph.so: argument checks, the choice of kernels
+// for each operation and format, workspace layout and the device status latch.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "morph_internal.cuh"
+
+namespace morph {
+
+// First device-side condition latched since the last morph_sync_status().
+__device__ int g_status;
+
+namespace {
+
+thread_local char t_err[512] = "";
+
+morph_status fail(morph_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(t_err, sizeof(t_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+morph_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(MORPH_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int word_bits(int fmt) { return fmt == MORPH_PACKED32 ? 32 : 64; }
+bool is_packed(int fmt) { return fmt == MORPH_PACKED32 || fmt == MORPH_PACKED64; }
+
+struct Range {
+    uintptr_t lo, hi;  // [lo, hi)
+};
+bool overlap(Range a, Range b) { return a.lo < b.hi && b.lo < a.hi && a.lo < a.hi && b.lo < b.hi; }
+
+Range packed_range(const morph_image *im) {
+    const int64_t bpw = word_bits(im->fmt) / 8;
+    const int64_t row_bytes = ((int64_t)im->width + word_bits(im->fmt) - 1) / word_bits(im->fmt) * bpw;
+    const uintptr_t lo = (uintptr_t)im->words;
+    return {lo, lo + (uintptr_t)(((int64_t)im->height - 1) * im->stride_words * bpw + row_bytes)};
+}
+
+morph_status check_image(const morph_image *im, const char *name) {
+    if (!im) return fail(MORPH_EINVAL, "%s is NULL", name);
+    if (im->reserved != 0) return fail(MORPH_EINVAL, "%s.reserved must be 0", name);
+    if (im->width < 1 || im->height < 1)
+        return fail(MORPH_EINVAL, "%s: width and height must be >= 1 (got %d x %d)", name,
+                    im->width, im->height);
+    if (is_packed(im->fmt)) {
+        const int B = word_bits(im->fmt);
+        if (!im->words) return fail(MORPH_EINVAL, "%s.words is NULL", name);
+        if ((uintptr_t)im->words % (B / 8))
+            return fail(MORPH_EINVAL, "%s.words is not aligned to %d bytes", name, B / 8);
+        if (im->stride_words < ((int64_t)im->width + B - 1) / B)
+            return fail(MORPH_EINVAL, "%s.stride_words %lld < ceil(width / %d)", name,
+                        (long long)im->stride_words, B);
+        return MORPH_OK;
+    }
+    if (im->fmt == MORPH_RLE) {
+        if (im->width > 65535)
+            return fail(MORPH_EINVAL, "%s: RLE width %d > 65535 (16-bit run ends)", name, im->width);
+        if (!im->row_ptr) return fail(MORPH_EINVAL, "%s.row_ptr is NULL", name);
+        if (im->capacity_runs < 0) return fail(MORPH_EINVAL, "%s.capacity_runs < 0", name);
+        if (im->capacity_runs > 0 && !im->runs) return fail(MORPH_EINVAL, "%s.runs is NULL", name);
+        return MORPH_OK;
+    }
+    return fail(MORPH_EINVAL, "%s.fmt %d is not a morph_format", name, im->fmt);
+}
+
+// Clip the rectangle to what can reach inside the image: a window side that
+// sticks out further than W-1 (H-1) pixels covers the same clipped pixels.
+struct Se {
+    int sw, sh, ox, oy;
+};
+Se clip_se(int W, int H, int sw, int sh, int ox, int oy) {
+    int l = ox, r = sw - 1 - ox, u = oy, d = sh - 1 - oy;
+    if (l > W - 1) l = W - 1;
+    if (r > W - 1) r = W - 1;
+    if (u > H - 1) u = H - 1;
+    if (d > H - 1) d = H - 1;
+    return {l + r + 1, u + d + 1, l, u};
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct RleWs {
+    size_t counts, tmp_nruns, tmp_rowptr, tmp_runs, total;
+    int64_t tmp_capacity;
+};
+
+RleWs rle_ws(int op, int W, int H) {
+    RleWs w;
+    w.counts = 0;
+    size_t off = align256((size_t)H * sizeof(int32_t));
+    w.tmp_capacity = 0;
+    w.tmp_nruns = w.tmp_rowptr = w.tmp_runs = off;
+    if (op == MORPH_OPEN || op == MORPH_CLOSE) {
+        w.tmp_capacity = (int64_t)H * ((W + 1) / 2);
+        w.tmp_nruns = off;
+        off += align256(sizeof(int64_t));
+        w.tmp_rowptr = off;
+        off += align256((size_t)(H + 1) * sizeof(int32_t));
+        w.tmp_runs = off;
+        off += align256((size_t)w.tmp_capacity * 2 * sizeof(uint16_t));
+    }
+    w.total = off;
+    return w;
+}
+
+morph_status check_op_args(int op, const morph_image *dst, const morph_image *src, int se_w,
+                           int se_h, int ox, int oy) {
+    morph_status st = check_image(src, "src");
+    if (st) return st;
+    if ((st = check_image(dst, "dst"))) return st;
+    if (op < MORPH_ERODE || op > MORPH_CLOSE) return fail(MORPH_EINVAL, "op %d is not a morph_op", op);
+    if (dst->width != src->width || dst->height != src->height)
+        return fail(MORPH_EINVAL, "dst is %d x %d but src is %d x %d", dst->width, dst->height,
+                    src->width, src->height);
+    if (is_packed(src->fmt) != is_packed(dst->fmt))
+        return fail(MORPH_EINVAL, "src and dst must both be packed or both be RLE");
+    if (se_w < 1 || se_h < 1 || se_w > 65535 || se_h > 65535)
+        return fail(MORPH_EINVAL, "structuring element %d x %d outside 1..65535", se_w, se_h);
+    if (ox < 0 || ox >= se_w || oy < 0 || oy >= se_h)
+        return fail(MORPH_EINVAL, "origin (%d, %d) outside the %d x %d rectangle", ox, oy, se_w, se_h);
+    if (is_packed(src->fmt)) {
+        if (overlap(packed_range(src), packed_range(dst))) return fail(MORPH_EINVAL, "dst overlaps src");
+    } else {
+        const Range srp{(uintptr_t)src->row_ptr, (uintptr_t)(src->row_ptr + src->height + 1)};
+        const Range drp{(uintptr_t)dst->row_ptr, (uintptr_t)(dst->row_ptr + dst->height + 1)};
+        const Range dru{(uintptr_t)dst->runs, (uintptr_t)(dst->runs + 2 * dst->capacity_runs)};
+        const Range sru{(uintptr_t)src->runs, (uintptr_t)(src->runs + 2 * src->capacity_runs)};
+        if (overlap(srp, drp) || overlap(srp, dru) || overlap(sru, drp) || overlap(sru, dru))
+            return fail(MORPH_EINVAL, "dst overlaps src");
+    }
+    return MORPH_OK;
+}
+
+// Horizontal reach of one fused launch (register window of 4 words).
+constexpr int MAX_REACH = 128;
+
+bool needs_chain(Se se) { return packed_halo(se.sw, se.ox) == 0; }
+
+int chain_passes(Se se) {
+    const int l = se.ox, r = se.sw - 1 - se.ox;
+    const int nl = (l + MAX_REACH - 1) / MAX_REACH, nr = (r + MAX_REACH - 1) / MAX_REACH;
+    return nl > nr ? nl : nr;
+}
+
+size_t packed_ws_bytes(int op, int W, int H, Se se) {
+    if (!needs_chain(se)) return 0;
+    const size_t img = align256((size_t)H * ((W + 31) / 32) * sizeof(uint32_t));
+    return (op == MORPH_OPEN || op == MORPH_CLOSE ? 3 : 2) * img;
+}
+
+struct PackedBuf {
+    const uint32_t *src;
+    int64_t sstride;
+    uint32_t *dst;
+    int64_t dstride;
+    int nw_cover;
+};
+
+cudaError_t packed_launch(int op, int W, int H, PackedBuf b, Se se, cudaStream_t s) {
+    PackedArgs a;
+    memset(&a, 0, sizeof(a));
+    a.src = b.src;
+    a.sstride = b.sstride;
+    a.dst = b.dst;
+    a.dstride = b.dstride;
+    a.W = W;
+    a.H = H;
+    a.nw_valid = (W + 31) / 32;
+    a.nw_cover = b.nw_cover;
+    if (packed_plan(a, op, se.sw, se.sh, se.ox, se.oy, 0, 0) != 0) return cudaErrorInvalidValue;
+    return launch_packed(a, s, 0);
+}
+
+// Erosion (or dilation) by a rectangle whose horizontal reach exceeds one
+// launch: the segment [-l, r] is the Minkowski sum of segments [-l_k, r_k]
+// (each containing 0, reach <= MAX_REACH); erosions by such segments compose
+// exactly under the clipped window, so the passes run one after the other
+// through scratch images; the vertical part rides on the last pass.
+cudaError_t packed_chain(int op, int W, int H, PackedBuf io, Se se, uint32_t *t0, uint32_t *t1,
+                         cudaStream_t s) {
+    const int n = chain_passes(se);
+    const int nwv = (W + 31) / 32;
+    int l = se.ox, r = se.sw - 1 - se.ox;
+    const uint32_t *in = io.src;
+    int64_t in_stride = io.sstride;
+    for (int k = 0; k < n; ++k) {
+        const int lk = l / (n - k), rk = r / (n - k);
+        l -= lk;
+        r -= rk;
+        const bool last = k == n - 1;
+        uint32_t *out = last ? io.dst : (k % 2 == 0 ? t0 : t1);
+        PackedBuf b{in, in_stride, out, last ? io.dstride : nwv, last ? io.nw_cover : nwv};
+        Se sk{lk + rk + 1, last ? se.sh : 1, lk, last ? se.oy : 0};
+        cudaError_t e = packed_launch(op, W, H, b, sk, s);
+        if (e != cudaSuccess) return e;
+        in = out;
+        in_stride = nwv;
+    }
+    return cudaSuccess;
+}
+
+morph_status run_packed(int op, const morph_image *dst, const morph_image *src, Se se, void *ws,
+                        size_t ws_bytes, cudaStream_t s) {
+    const int W = src->width, H = src->height;
+    PackedBuf io{(const uint32_t *)src->words, src->stride_words * (word_bits(src->fmt) / 32),
+                 (uint32_t *)dst->words, dst->stride_words * (word_bits(dst->fmt) / 32),
+                 dst->fmt == MORPH_PACKED32 ? (W + 31) / 32 : 2 * ((W + 63) / 64)};
+    cudaError_t e;
+    if (!needs_chain(se)) {
+        e = packed_launch(op, W, H, io, se, s);
+    } else {
+        const size_t need = packed_ws_bytes(op, W, H, se);
+        if (!ws || ws_bytes < need)
+            return fail(MORPH_ENOMEM, "a %d-pixel-wide rectangle needs %zu bytes of workspace, got %zu",
+                        se.sw, need, ws ? ws_bytes : (size_t)0);
+        const size_t img = need / (op == MORPH_OPEN || op == MORPH_CLOSE ? 3 : 2);
+        uint32_t *t0 = (uint32_t *)ws, *t1 = (uint32_t *)((char *)ws + img);
+        if (op == MORPH_ERODE || op == MORPH_DILATE) {
+            e = packed_chain(op, W, H, io, se, t0, t1, s);
+        } else {
+            const int nwv = (W + 31) / 32;
+            uint32_t *mid = (uint32_t *)((char *)ws + 2 * img);
+            const int first = op == MORPH_OPEN ? MORPH_ERODE : MORPH_DILATE;
+            const int second = op == MORPH_OPEN ? MORPH_DILATE : MORPH_ERODE;
+            PackedBuf a{io.src, io.sstride, mid, nwv, nwv};
+            e = packed_chain(first, W, H, a, se, t0, t1, s);
+            if (e == cudaSuccess) {
+                PackedBuf b{mid, nwv, io.dst, io.dstride, io.nw_cover};
+                e = packed_chain(second, W, H, b, se, t0, t1, s);
+            }
+        }
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "packed morphology launch");
+    return MORPH_OK;
+}
+
+RleIn rle_in(const morph_image *im) {
+    return {im->row_ptr, im->runs, im->width, im->height};
+}
+RleOut rle_out(const morph_image *im) {
+    return {im->row_ptr, im->runs, im->capacity_runs, im->n_runs};
+}
+
+morph_status run_rle(int op, const morph_image *dst, const morph_image *src, Se se, void *ws,
+                     size_t ws_bytes, cudaStream_t s) {
+    const int W = src->width, H = src->height;
+    const RleWs L = rle_ws(op, W, H);
+    if (!ws || ws_bytes < L.total)
+        return fail(MORPH_ENOMEM, "workspace of %zu bytes is smaller than the %zu bytes needed",
+                    ws ? ws_bytes : (size_t)0, L.total);
+    char *base = (char *)ws;
+    int32_t *counts = (int32_t *)(base + L.counts);
+    int *st = device_status_ptr();
+    cudaError_t e;
+    if (op == MORPH_ERODE || op == MORPH_DILATE) {
+        e = launch_rle_rect(rle_in(src), rle_out(dst), op == MORPH_DILATE, se.sw, se.sh, se.ox,
+                            se.oy, counts, st, s);
+    } else {
+        RleOut tmp{(int32_t *)(base + L.tmp_rowptr), (uint16_t *)(base + L.tmp_runs),
+                   L.tmp_capacity, (int64_t *)(base + L.tmp_nruns)};
+        const int first_dilate = op == MORPH_CLOSE;
+        e = launch_rle_rect(rle_in(src), tmp, first_dilate, se.sw, se.sh, se.ox, se.oy, counts,
+                            st, s);
+        if (e == cudaSuccess) {
+            RleIn tin{tmp.row_ptr, tmp.runs, W, H};
+            e = launch_rle_rect(tin, rle_out(dst), !first_dilate, se.sw, se.sh, se.ox, se.oy,
+                                counts, st, s);
+        }
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "RLE morphology launch");
+    return MORPH_OK;
+}
+
+}  // namespace
+
+int *device_status_ptr() {
+    static std::mutex mu;
+    static int *ptrs[128] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ptrs[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_status) == cudaSuccess) ptrs[dev] = (int *)p;
+    }
+    return ptrs[dev];
+}
+
+}  // namespace morph
+
+using namespace morph;
+
+extern "C" {
+
+morph_status morph_rect(int op, const morph_image *dst, const morph_image *src, int se_w, int se_h,
+                        int origin_x, int origin_y, void *workspace, size_t workspace_bytes,
+                        void *stream) {
+    morph_status st = check_op_args(op, dst, src, se_w, se_h, origin_x, origin_y);
+    if (st) return st;
+    const Se se = clip_se(src->width, src->height, se_w, se_h, origin_x, origin_y);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (is_packed(src->fmt)) return run_packed(op, dst, src, se, workspace, workspace_bytes, s);
+    return run_rle(op, dst, src, se, workspace, workspace_bytes, s);
+}
+
+morph_status morph_erode_rect(const morph_image *dst, const morph_image *src, int se_w, int se_h,
+                              int origin_x, int origin_y, void *workspace,
+                              size_t workspace_bytes, void *stream) {
+    return morph_rect(MORPH_ERODE, dst, src, se_w, se_h, origin_x, origin_y, workspace,
+                      workspace_bytes, stream);
+}
+
+morph_status morph_dilate_rect(const morph_image *dst, const morph_image *src, int se_w, int se_h,
+                               int origin_x, int origin_y, void *workspace,
+                               size_t workspace_bytes, void *stream) {
+    return morph_rect(MORPH_DILATE, dst, src, se_w, se_h, origin_x, origin_y, workspace,
+                      workspace_bytes, stream);
+}
+
+morph_status morph_open_rect(const morph_image *dst, const morph_image *src, int se_w, int se_h,
+                             int origin_x, int origin_y, void *workspace, size_t workspace_bytes,
+                             void *stream) {
+    return morph_rect(MORPH_OPEN, dst, src, se_w, se_h, origin_x, origin_y, workspace,
+                      workspace_bytes, stream);
+}
+
+morph_status morph_close_rect(const morph_image *dst, const morph_image *src, int se_w, int se_h,
+                              int origin_x, int origin_y, void *workspace,
+                              size_t workspace_bytes, void *stream) {
+    return morph_rect(MORPH_CLOSE, dst, src, se_w, se_h, origin_x, origin_y, workspace,
+                      workspace_bytes, stream);
+}
+
+size_t morph_workspace_size(int op, const morph_image *dst, const morph_image *src, int se_w,
+                            int se_h, int origin_x, int origin_y) {
+    (void)dst;
+    if (!src || src->width < 1 || src->height < 1 || se_w < 1 || se_h < 1 || origin_x < 0 ||
+        origin_x >= se_w || origin_y < 0 || origin_y >= se_h)
+        return 0;
+    if (is_packed(src->fmt)) {
+        const Se se = clip_se(src->width, src->height, se_w, se_h, origin_x, origin_y);
+        return packed_ws_bytes(op, src->width, src->height, se);
+    }
+    return rle_ws(op, src->width, src->height).total;
+}
+
+size_t morph_convert_workspace_size(int height) {
+    return height < 1 ? 0 : align256((size_t)height * sizeof(int32_t));
+}
+
+morph_status rle_from_bitmap(const morph_image *dst_rle, const morph_image *src_packed,
+                             void *workspace, size_t workspace_bytes, void *stream) {
+    morph_status st = check_image(src_packed, "src");
+    if (st) return st;
+    if ((st = check_image(dst_rle, "dst"))) return st;
+    if (!is_packed(src_packed->fmt) || dst_rle->fmt != MORPH_RLE)
+        return fail(MORPH_EINVAL, "rle_from_bitmap needs a packed src and an RLE dst");
+    if (dst_rle->width != src_packed->width || dst_rle->height != src_packed->height)
+        return fail(MORPH_EINVAL, "dst and src sizes differ");
+    const size_t need = morph_convert_workspace_size(src_packed->height);
+    if (!workspace || workspace_bytes < need)
+        return fail(MORPH_ENOMEM, "workspace of %zu bytes is smaller than the %zu bytes needed",
+                    workspace ? workspace_bytes : (size_t)0, need);
+    const Range src_r = packed_range(src_packed);
+    const Range drp{(uintptr_t)dst_rle->row_ptr, (uintptr_t)(dst_rle->row_ptr + dst_rle->height + 1)};
+    const Range dru{(uintptr_t)dst_rle->runs, (uintptr_t)(dst_rle->runs + 2 * dst_rle->capacity_runs)};
+    if (overlap(src_r, drp) || overlap(src_r, dru)) return fail(MORPH_EINVAL, "dst overlaps src");
+    cudaError_t e = launch_rle_from_bitmap(
+        (const uint32_t *)src_packed->words, src_packed->stride_words * (word_bits(src_packed->fmt) / 32),
+        src_packed->width, src_packed->height, rle_out(dst_rle), (int32_t *)workspace,
+        device_status_ptr(), (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "rle_from_bitmap launch");
+    return MORPH_OK;
+}
+
+morph_status rle_to_bitmap(const morph_image *dst_packed, const morph_image *src_rle, void *stream) {
+    morph_status st = check_image(src_rle, "src");
+    if (st) return st;
+    if ((st = check_image(dst_packed, "dst"))) return st;
+    if (src_rle->fmt != MORPH_RLE || !is_packed(dst_packed->fmt))
+        return fail(MORPH_EINVAL, "rle_to_bitmap needs an RLE src and a packed dst");
+    if (dst_packed->width != src_rle->width || dst_packed->height != src_rle->height)
+        return fail(MORPH_EINVAL, "dst and src sizes differ");
+    const Range dst_r = packed_range(dst_packed);
+    const Range srp{(uintptr_t)src_rle->row_ptr, (uintptr_t)(src_rle->row_ptr + src_rle->height + 1)};
+    const Range sru{(uintptr_t)src_rle->runs, (uintptr_t)(src_rle->runs + 2 * src_rle->capacity_runs)};
+    if (overlap(dst_r, srp) || overlap(dst_r, sru)) return fail(MORPH_EINVAL, "dst overlaps src");
+    const int W = dst_packed->width;
+    const int nw_cover = dst_packed->fmt == MORPH_PACKED32 ? (W + 31) / 32 : 2 * ((W + 63) / 64);
+    cudaError_t e = launch_rle_to_bitmap(rle_in(src_rle), (uint32_t *)dst_packed->words,
+                                         dst_packed->stride_words * (word_bits(dst_packed->fmt) / 32),
+                                         nw_cover, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "rle_to_bitmap launch");
+    return MORPH_OK;
+}
+
+morph_status morph_sync_status(void *stream) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    int *p = device_status_ptr();
+    if (!p) return fail(MORPH_ECUDA, "device status word unavailable");
+    int code = 0;
+    e = cudaMemcpy(&code, p, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (code) {
+        const int zero = 0;
+        e = cudaMemcpy(p, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "status clear");
+        return fail((morph_status)code, "device reported %s", morph_status_string(code));
+    }
+    return MORPH_OK;
+}
+
+const char *morph_last_error(void) { return t_err; }
+
+const char *morph_status_string(int status) {
+    switch (status) {
+    case MORPH_OK: return "MORPH_OK";
+    case MORPH_EINVAL: return "MORPH_EINVAL";
+    case MORPH_ECAPACITY: return "MORPH_ECAPACITY";
+    case MORPH_ENOMEM: return "MORPH_ENOMEM";
+    case MORPH_ECUDA: return "MORPH_ECUDA";
+    case MORPH_ETIMEOUT: return "MORPH_ETIMEOUT";
+    default: return "unknown morph_status";
+    }
+}
+
+int morph_abi_version(void) { return MORPH_ABI_VERSION; }
+
+}  // extern "C"

@@ -1,0 +1,286 @@
+"""Python binding of ``libmorph.so`` (the C ABI in ``include/morph.h``).
+
+Argument marshalling only: every pixel of every operation is computed by the
+CUDA kernels behind the ABI.  PyTorch supplies device memory (tensors) and
+streams.  Importing this module loads the library and raises if it has not
+been built — there is no fallback path.
+
+Images:
+  * :class:`Packed` — a torch tensor of shape ``[H, stride_words]`` with dtype
+    ``torch.int32`` (``MORPH_PACKED32``) or ``torch.int64``
+    (``MORPH_PACKED64``) holding little-endian bit rows;
+  * :class:`Rle` — ``row_ptr`` (int32 ``[H+1]``), ``runs`` (int16 ``[cap, 2]``
+    holding uint16 start/end pairs), ``n_runs`` (int64 ``[1]``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmorph.so")
+
+MORPH_OK, MORPH_EINVAL, MORPH_ECAPACITY, MORPH_ENOMEM, MORPH_ECUDA, MORPH_ETIMEOUT = range(6)
+PACKED32, PACKED64, RLE = 0, 1, 2
+ERODE, DILATE, OPEN, CLOSE = 0, 1, 2, 3
+OPS = {"erode": ERODE, "dilate": DILATE, "open": OPEN, "close": CLOSE}
+PATH_PACKED, PATH_RLE = 0, 1
+
+
+class MorphError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (_status_name(status), message))
+        self.status = status
+
+
+class morph_image(ctypes.Structure):
+    _fields_ = [
+        ("fmt", ctypes.c_int32),
+        ("width", ctypes.c_int32),
+        ("height", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("words", ctypes.c_void_p),
+        ("stride_words", ctypes.c_int64),
+        ("row_ptr", ctypes.c_void_p),
+        ("runs", ctypes.c_void_p),
+        ("capacity_runs", ctypes.c_int64),
+        ("n_runs", ctypes.c_void_p),
+    ]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libmorph.so is not built (run __graft_entry__.build() or "
+                          "python -m paper_0712_0121_gb300.build); there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    img_p = ctypes.POINTER(morph_image)
+    vp, sz, ci = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int
+    for name in ("morph_erode_rect", "morph_dilate_rect", "morph_open_rect", "morph_close_rect"):
+        f = getattr(lib, name)
+        f.argtypes = [img_p, img_p, ci, ci, ci, ci, vp, sz, vp]
+        f.restype = ci
+    lib.morph_rect.argtypes = [ci, img_p, img_p, ci, ci, ci, ci, vp, sz, vp]
+    lib.morph_rect.restype = ci
+    lib.morph_workspace_size.argtypes = [ci, img_p, img_p, ci, ci, ci, ci]
+    lib.morph_workspace_size.restype = sz
+    lib.morph_convert_workspace_size.argtypes = [ci]
+    lib.morph_convert_workspace_size.restype = sz
+    lib.rle_from_bitmap.argtypes = [img_p, img_p, vp, sz, vp]
+    lib.rle_from_bitmap.restype = ci
+    lib.rle_to_bitmap.argtypes = [img_p, img_p, vp]
+    lib.rle_to_bitmap.restype = ci
+    lib.morph_sync_status.argtypes = [vp]
+    lib.morph_sync_status.restype = ci
+    lib.morph_last_error.argtypes = []
+    lib.morph_last_error.restype = ctypes.c_char_p
+    lib.morph_status_string.argtypes = [ci]
+    lib.morph_status_string.restype = ctypes.c_char_p
+    lib.morph_abi_version.argtypes = []
+    lib.morph_abi_version.restype = ci
+    return lib
+
+
+_lib = _load()
+
+
+def lib() -> ctypes.CDLL:
+    return _lib
+
+
+def _status_name(st: int) -> str:
+    return _lib.morph_status_string(st).decode()
+
+
+def _check(st: int) -> None:
+    if st != MORPH_OK:
+        raise MorphError(st, _lib.morph_last_error().decode())
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+# --------------------------------------------------------------- images
+
+class Packed:
+    """A packed bitmap on the device: ``words`` is ``[H, stride]`` int32/int64."""
+
+    def __init__(self, words: torch.Tensor, width: int):
+        if words.dtype not in (torch.int32, torch.int64) or words.dim() != 2:
+            raise ValueError("words must be a 2D int32 or int64 tensor")
+        self.words = words
+        self.width = int(width)
+        self.height = int(words.shape[0])
+        self.fmt = PACKED32 if words.dtype == torch.int32 else PACKED64
+
+    @property
+    def word_bits(self) -> int:
+        return 32 if self.fmt == PACKED32 else 64
+
+    @staticmethod
+    def empty(width: int, height: int, word_bits: int = 64, device="cuda", stride=None) -> "Packed":
+        dt = torch.int32 if word_bits == 32 else torch.int64
+        nw = (width + word_bits - 1) // word_bits
+        stride = nw if stride is None else stride
+        return Packed(torch.empty((height, stride), dtype=dt, device=device), width)
+
+    def desc(self) -> morph_image:
+        d = morph_image()
+        d.fmt, d.width, d.height, d.reserved = self.fmt, self.width, self.height, 0
+        d.words = self.words.data_ptr()
+        d.stride_words = self.words.stride(0)
+        return d
+
+
+class Rle:
+    """A run-length image on the device (CSR of uint16 (start, end) runs)."""
+
+    def __init__(self, row_ptr: torch.Tensor, runs: torch.Tensor, width: int,
+                 n_runs: torch.Tensor | None = None):
+        self.row_ptr = row_ptr
+        self.runs = runs
+        self.width = int(width)
+        self.height = int(row_ptr.shape[0]) - 1
+        self.n_runs = n_runs if n_runs is not None else torch.zeros(1, dtype=torch.int64,
+                                                                    device=row_ptr.device)
+        self.fmt = RLE
+
+    @property
+    def capacity(self) -> int:
+        return int(self.runs.shape[0])
+
+    @staticmethod
+    def empty(width: int, height: int, capacity: int, device="cuda") -> "Rle":
+        return Rle(torch.zeros(height + 1, dtype=torch.int32, device=device),
+                   torch.empty((max(capacity, 1), 2), dtype=torch.int16, device=device), width)
+
+    def desc(self) -> morph_image:
+        d = morph_image()
+        d.fmt, d.width, d.height, d.reserved = RLE, self.width, self.height, 0
+        d.row_ptr = self.row_ptr.data_ptr()
+        d.runs = self.runs.data_ptr()
+        d.capacity_runs = self.capacity
+        d.n_runs = self.n_runs.data_ptr()
+        return d
+
+    def to_numpy(self):
+        """(row_ptr int32[H+1], runs uint16[N, 2]) on the host (synchronises)."""
+        rp = self.row_ptr.cpu().numpy()
+        n = int(rp[-1])
+        runs = self.runs[:n].cpu().numpy().view(np.uint16).reshape(-1, 2)
+        return rp, runs
+
+    @staticmethod
+    def from_numpy(row_ptr, runs, width, device="cuda", capacity=None) -> "Rle":
+        rp = torch.as_tensor(np.ascontiguousarray(row_ptr, dtype=np.int32), device=device)
+        r = np.ascontiguousarray(runs, dtype=np.uint16).reshape(-1, 2)
+        cap = max(capacity or r.shape[0], 1)
+        buf = np.zeros((cap, 2), dtype=np.uint16)
+        buf[: r.shape[0]] = r
+        rt = torch.as_tensor(buf.view(np.int16), device=device)
+        n = torch.tensor([r.shape[0]], dtype=torch.int64, device=device)
+        return Rle(rp, rt, width, n)
+
+
+# ---------------------------------------------------------------- layout
+
+def pack(img, word_bits: int = 64, device="cuda", stride=None) -> Packed:
+    """0/1 ``uint8[H, W]`` array -> :class:`Packed` (LSB-first rows)."""
+    a = np.ascontiguousarray(img, dtype=np.uint8)
+    H, W = a.shape
+    nw = (W + word_bits - 1) // word_bits
+    stride = nw if stride is None else stride
+    b = np.packbits(a, axis=1, bitorder="little")
+    rowbytes = stride * word_bits // 8
+    out = np.zeros((H, rowbytes), dtype=np.uint8)
+    out[:, : b.shape[1]] = b
+    dt = np.int32 if word_bits == 32 else np.int64
+    t = torch.from_numpy(out.view(dt).reshape(H, stride).copy())
+    return Packed(t.to(device), W)
+
+
+def unpack(p: Packed) -> np.ndarray:
+    """:class:`Packed` -> 0/1 ``uint8[H, W]`` on the host (synchronises)."""
+    raw = p.words.cpu().numpy().view(np.uint8).reshape(p.height, -1)
+    return np.unpackbits(raw, axis=1, bitorder="little")[:, : p.width].copy()
+
+
+# ------------------------------------------------------------ operations
+
+def workspace_size(op, dst, src, se_w: int, se_h: int, origin_x=None, origin_y=None) -> int:
+    ox = se_w // 2 if origin_x is None else origin_x
+    oy = se_h // 2 if origin_y is None else origin_y
+    return int(_lib.morph_workspace_size(OPS.get(op, op), ctypes.byref(dst.desc()),
+                                         ctypes.byref(src.desc()), se_w, se_h, ox, oy))
+
+
+def _ws_args(workspace):
+    if workspace is None:
+        return None, 0
+    return workspace.data_ptr(), workspace.numel() * workspace.element_size()
+
+
+def morph_rect(op, dst, src, se_w: int, se_h: int, origin_x=None, origin_y=None,
+               workspace: torch.Tensor | None = None, stream=None) -> None:
+    """Erode / dilate / open / close ``src`` into ``dst`` (same family of
+    format).  Origin defaults to the centre (se_w // 2, se_h // 2).  When the
+    operation needs a workspace and none is given, one is allocated here."""
+    ox = se_w // 2 if origin_x is None else origin_x
+    oy = se_h // 2 if origin_y is None else origin_y
+    opc = OPS.get(op, op)
+    if workspace is None:
+        n = workspace_size(opc, dst, src, se_w, se_h, ox, oy)
+        if n:
+            dev = src.row_ptr.device if src.fmt == RLE else src.words.device
+            workspace = torch.empty(n, dtype=torch.uint8, device=dev)
+    wp, wn = _ws_args(workspace)
+    _check(_lib.morph_rect(opc, ctypes.byref(dst.desc()), ctypes.byref(src.desc()), se_w, se_h,
+                           ox, oy, wp, wn, _stream_handle(stream)))
+
+
+def morph_erode_rect(dst, src, se_w, se_h, origin_x=None, origin_y=None, workspace=None, stream=None):
+    morph_rect(ERODE, dst, src, se_w, se_h, origin_x, origin_y, workspace, stream)
+
+
+def morph_dilate_rect(dst, src, se_w, se_h, origin_x=None, origin_y=None, workspace=None, stream=None):
+    morph_rect(DILATE, dst, src, se_w, se_h, origin_x, origin_y, workspace, stream)
+
+
+def morph_open_rect(dst, src, se_w, se_h, origin_x=None, origin_y=None, workspace=None, stream=None):
+    morph_rect(OPEN, dst, src, se_w, se_h, origin_x, origin_y, workspace, stream)
+
+
+def morph_close_rect(dst, src, se_w, se_h, origin_x=None, origin_y=None, workspace=None, stream=None):
+    morph_rect(CLOSE, dst, src, se_w, se_h, origin_x, origin_y, workspace, stream)
+
+
+def convert_workspace_size(height: int) -> int:
+    return int(_lib.morph_convert_workspace_size(height))
+
+
+def rle_from_bitmap(dst: Rle, src: Packed, workspace: torch.Tensor | None = None, stream=None) -> None:
+    if workspace is None:
+        workspace = torch.empty(max(convert_workspace_size(src.height), 1), dtype=torch.uint8,
+                                device=src.words.device)
+    wp, wn = _ws_args(workspace)
+    _check(_lib.rle_from_bitmap(ctypes.byref(dst.desc()), ctypes.byref(src.desc()), wp, wn,
+                                _stream_handle(stream)))
+
+
+def rle_to_bitmap(dst: Packed, src: Rle, stream=None) -> None:
+    _check(_lib.rle_to_bitmap(ctypes.byref(dst.desc()), ctypes.byref(src.desc()),
+                              _stream_handle(stream)))
+
+
+def sync_status(stream=None) -> int:
+    """Wait for the stream; return the latched device status (and clear it)."""
+    return int(_lib.morph_sync_status(_stream_handle(stream)))
+
+
+def abi_version() -> int:
+    return int(_lib.morph_abi_version())

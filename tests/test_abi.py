@@ -1,0 +1,109 @@
+"""CPU-only checks of the C ABI: the library loads, exports every function
+that ``include/morph.h`` declares, and rejects bad arguments on the host
+before any device work (no GPU call is made by these tests)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def M():
+    from paper_0712_0121_gb300 import build
+    build.build_morph()
+    from paper_0712_0121_gb300 import morph
+    return morph
+
+
+def declared_functions():
+    names = []
+    for f in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if f.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", f)).read()
+            text = "\n".join(l for l in text.splitlines() if not l.lstrip().startswith("#"))
+            names += re.findall(r"MORPH_API\s+[\w\s\*]*?\b(\w+)\s*\(", text)
+    return names
+
+
+def test_header_declares_the_api():
+    names = declared_functions()
+    for n in ("morph_erode_rect", "morph_dilate_rect", "morph_open_rect", "morph_close_rect",
+              "rle_from_bitmap", "rle_to_bitmap"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(M):
+    lib = ctypes.CDLL(M.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert M.abi_version() == 1
+
+
+def _img(M, fmt=1, W=100, H=10, words=0x10000, stride=2):
+    d = M.morph_image()
+    d.fmt, d.width, d.height, d.reserved = fmt, W, H, 0
+    d.words = words
+    d.stride_words = stride
+    return d
+
+
+def _call(M, op, dst, src, sw=3, sh=3, ox=1, oy=1, ws=None, nws=0):
+    return M.lib().morph_rect(op, ctypes.byref(dst) if dst is not None else None,
+                              ctypes.byref(src) if src is not None else None, sw, sh, ox, oy, ws,
+                              nws, None)
+
+
+def test_host_argument_checks(M):
+    src = _img(M, words=0x10000)
+    dst = _img(M, words=0x90000)
+    E = M.MORPH_EINVAL
+    assert _call(M, 0, None, src) == E
+    assert _call(M, 0, dst, None) == E
+    assert _call(M, 7, dst, src) == E                      # op
+    assert _call(M, 0, dst, src, sw=0) == E                # SE size
+    assert _call(M, 0, dst, src, sw=3, ox=3) == E          # origin outside
+    assert _call(M, 0, dst, src, sh=2, oy=-1) == E
+    bad = _img(M, words=0x90000, W=99)
+    assert _call(M, 0, bad, src) == E                      # size mismatch
+    alias = _img(M, words=0x10008)
+    assert _call(M, 0, alias, src) == E                    # overlap
+    short = _img(M, words=0x90000, stride=1)
+    assert _call(M, 0, short, src) == E                    # stride < ceil(W/64)
+    mis = _img(M, words=0x90004)
+    assert _call(M, 0, mis, src) == E                      # 64-bit words not aligned
+    res = _img(M, words=0x90000)
+    res.reserved = 1
+    assert _call(M, 0, res, src) == E
+    assert b"reserved" in M.lib().morph_last_error()
+
+
+def test_rle_checks_and_workspace(M):
+    def rle(W=100, H=10, rp=0x1000, runs=0x2000, cap=100):
+        d = M.morph_image()
+        d.fmt, d.width, d.height = 2, W, H
+        d.row_ptr, d.runs, d.capacity_runs = rp, runs, cap
+        return d
+    src, dst = rle(), rle(rp=0x5000, runs=0x6000)
+    assert _call(M, 0, dst, src) == M.MORPH_ENOMEM               # no workspace
+    need = M.lib().morph_workspace_size(2, ctypes.byref(dst), ctypes.byref(src), 3, 3, 1, 1)
+    assert need >= 10 * 4
+    assert _call(M, 2, dst, src, ws=0x900000, nws=need - 1) == M.MORPH_ENOMEM
+    wide = rle(W=70000)
+    assert _call(M, 0, rle(W=70000, rp=0x5000, runs=0x6000), wide) == M.MORPH_EINVAL
+    assert _call(M, 0, rle(rp=0x1004, runs=0x6000), src) == M.MORPH_EINVAL  # row_ptr overlap
+    mixed = _img(M, words=0x90000)
+    assert _call(M, 0, mixed, src) == M.MORPH_EINVAL              # packed dst, RLE src
+
+
+def test_packed_workspace_only_for_wide_rectangles(M):
+    src = _img(M, W=5000, stride=79)
+    dst = _img(M, W=5000, stride=79, words=0x9000000)
+    f = M.lib().morph_workspace_size
+    assert f(0, ctypes.byref(dst), ctypes.byref(src), 257, 3, 128, 1) == 0
+    assert f(0, ctypes.byref(dst), ctypes.byref(src), 259, 3, 129, 1) > 0
+    assert f(2, ctypes.byref(dst), ctypes.byref(src), 600, 1, 0, 0) > 0
+    small = _img(M, W=100)
+    assert f(0, ctypes.byref(_img(M, W=100, words=0x9000000)), ctypes.byref(small), 600, 1, 0, 0) == 0

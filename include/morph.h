@@ -171,6 +171,64 @@ MORPH_API morph_status rle_from_bitmap(const morph_image *dst_rle, const morph_i
 MORPH_API morph_status rle_to_bitmap(const morph_image *dst_packed, const morph_image *src_rle,
                            void *stream);
 
+/* ----------------------------------------------------------------- batch --
+ * Many uneven pages, each with its own op, rectangle and path, in ONE
+ * persistent kernel launch.  A job reads a packed src page and writes a
+ * packed dst page (same size, no overlap).  path MORPH_PATH_PACKED runs the
+ * fused tile kernel on the page; MORPH_PATH_RLE converts the page to runs,
+ * runs the RLE operation and converts back, all inside the same launch.  The
+ * choice per page is the caller's (the Python autotuner picks it by ink
+ * density and rectangle).
+ *
+ * Use: morph_batch_plan_bytes() -> a host buffer; morph_batch_plan_build()
+ * fills it (all checks happen here); the caller copies the plan to device
+ * memory and calls morph_batch_launch() with that copy, the host plan and a
+ * workspace of morph_batch_workspace_size() bytes (counters and the RLE
+ * buffers of RLE-path jobs).  The launch does no host work beyond one memset
+ * of the counters and the kernel launch, so it can be captured in a CUDA
+ * graph and replayed while the plan, workspace and pages stay valid.
+ * Work items are claimed from a device queue in plan order; an item waits
+ * (bounded spin, acquire loads) only for items of smaller index, which are
+ * already held by running CTAs, so the launch cannot deadlock.  A wait longer
+ * than the plan's limit (4 s) latches MORPH_ETIMEOUT and stops every CTA; an RLE buffer that is
+ * too small latches MORPH_ECAPACITY and leaves that job's dst unwritten.
+ *
+ * tile_rows: row-band height of packed tiles (0 = default).
+ * rle_runs_per_row: room per row in each RLE buffer of RLE-path jobs
+ * (0 = W/16 + 4, at most ceil(W/2)).
+ * Limits: packed-path rectangles must reach <= 128 pixels left and right of
+ * the origin after clipping; RLE-path pages must be <= 65535 pixels wide.
+ */
+typedef enum morph_path { MORPH_PATH_PACKED = 0, MORPH_PATH_RLE = 1 } morph_path;
+
+typedef struct morph_job {
+    int32_t op;          /* morph_op */
+    int32_t path;        /* morph_path */
+    int32_t se_w, se_h, origin_x, origin_y;
+    morph_image src;     /* packed */
+    morph_image dst;     /* packed, same size */
+} morph_job;
+
+MORPH_API size_t morph_batch_plan_bytes(const morph_job *jobs, int n_jobs, int tile_rows,
+                                        int rle_runs_per_row);
+MORPH_API morph_status morph_batch_plan_build(void *host_plan, size_t plan_bytes,
+                                              const morph_job *jobs, int n_jobs, int tile_rows,
+                                              int rle_runs_per_row);
+MORPH_API size_t morph_batch_workspace_size(const void *host_plan);
+/* Number of work items in a plan (-1 for an invalid plan). */
+MORPH_API int morph_batch_items(const void *host_plan);
+/* Test hook on a host plan (before it is copied to the device):
+ * what = 0: set the wait limit to `value` ns (>= 1 ms; default 4 s);
+ * what = 1: add `value` to the item count that the second phase of the first
+ *           multi-phase (RLE-path) job waits for, so that its wait runs out —
+ *           used to check that MORPH_ETIMEOUT is reported and the device stays
+ *           usable. */
+MORPH_API morph_status morph_batch_plan_debug(void *host_plan, int what, long long value);
+/* n_ctas <= 0: as many CTAs as fit on the device at once. */
+MORPH_API morph_status morph_batch_launch(const void *dev_plan, const void *host_plan,
+                                          void *workspace, size_t workspace_bytes, int n_ctas,
+                                          void *stream);
+
 /* ---------------------------------------------------------------- status -- */
 /* Wait for `stream`, then return (and clear) the first device-side condition
  * latched since the last call (MORPH_ECAPACITY, MORPH_ETIMEOUT), else the

@@ -175,7 +175,7 @@ cudaError_t packed_launch(int op, int W, int H, PackedBuf b, Se se, cudaStream_t
     a.nw_valid = (W + 31) / 32;
     a.nw_cover = b.nw_cover;
     if (packed_plan(a, op, se.sw, se.sh, se.ox, se.oy, 0, 0) != 0) return cudaErrorInvalidValue;
-    return launch_packed(a, s, 0);
+    return launch_packed(a, s);
 }
 
 // Erosion (or dilation) by a rectangle whose horizontal reach exceeds one
@@ -279,6 +279,13 @@ morph_status run_rle(int op, const morph_image *dst, const morph_image *src, Se 
 }
 
 }  // namespace
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(t_err, sizeof(t_err), fmt, ap);
+    va_end(ap);
+}
 
 int *device_status_ptr() {
     static std::mutex mu;

@@ -1,0 +1,597 @@
+// Persistent batch launch (K8): many uneven pages, each with its own
+// operation, rectangle and path, in ONE kernel launch.
+//
+// The host builds a plan: a job table and a list of work items.  A packed
+// job is one phase of independent tiles (the fused tile of packed_tile.cuh).
+// An RLE job is a chain of phases — bitmap->RLE count, scan, write; per
+// erosion stage the run pass or between-line pass count, scan, write; RLE->
+// bitmap — whose items depend on every item of the job's previous phase.
+// Items are listed phase-major and claimed in list order from a device queue
+// by persistent CTAs.  An item waits (bounded spin with acquire loads) only
+// for items of smaller index, which running CTAs have already claimed, so
+// the launch cannot deadlock; a wait that exceeds the time limit latches
+// MORPH_ETIMEOUT and makes every CTA stop.
+//
+// The kernel reads the plan from device memory (the caller copies it there)
+// and keeps its counters and RLE buffers in the caller's workspace, so one
+// launch can be captured in a CUDA graph and replayed.
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "packed_tile.cuh"
+#include "rle_tile.cuh"
+
+namespace morph {
+namespace {
+
+constexpr uint32_t PLAN_MAGIC = 0x4d425031u;  // "MBP1"
+constexpr int MAX_PH = 11;
+constexpr int BATCH_THREADS = 256;
+constexpr long long WAIT_LIMIT_NS = 4000000000ll;  // default 4 s
+
+enum ItemKind : int {
+    IK_PACKED = 0,
+    IK_B2R_COUNT,
+    IK_SCAN,
+    IK_B2R_WRITE,
+    IK_ROW_COUNT,
+    IK_ROW_WRITE,
+    IK_V_COUNT,
+    IK_V_WRITE,
+    IK_R2B,
+};
+
+struct BatchJob {
+    int32_t path;               // MORPH_PATH_PACKED / MORPH_PATH_RLE
+    int32_t variant;            // packed tile variant
+    int32_t nphase;
+    int32_t phase_items[MAX_PH];
+    int32_t phase_kind[MAX_PH];
+    int32_t phase_stage[MAX_PH];  // erosion stage (0/1) of run / between-line phases
+    int32_t gx;                 // packed: tiles along x of the grid
+    PackedArgs pa;              // packed path
+    // RLE path
+    const uint32_t *src;
+    int64_t sstride;
+    uint32_t *dst;
+    int64_t dstride;
+    int32_t W, H, nw_cover, nst;
+    RowOp rop[2];
+    VArgs va[2];                // pointers are filled on the device from ws offsets
+    int32_t vkind[2];           // between-line variant (nwt, kmax)
+    int64_t off_counts, off_rpA, off_runsA, off_rpB, off_runsB, off_nA, off_nB;
+    int64_t cap;                // runs capacity of each RLE buffer
+};
+
+struct BatchItem {
+    int32_t job;
+    int16_t phase;
+    int16_t kind;
+    int32_t idx;
+};
+
+struct BatchHeader {
+    uint32_t magic;
+    int32_t n_jobs, n_items, smem_bytes;
+    int64_t jobs_off, items_off, plan_bytes;
+    int64_t ws_ctrl_bytes, ws_bytes;
+    int64_t wait_limit_ns;
+};
+
+size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ---------------------------------------------------------- device side
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Thread 0: wait until *ctr >= target.  false on abort or time-out.
+__device__ bool wait_count(const int *ctr, int target, int *abort_flag, int *status,
+                           unsigned long long limit_ns) {
+    const unsigned long long t0 = now_ns();
+    for (unsigned it = 0;; ++it) {
+        if (ld_acquire(ctr) >= target) return true;
+        if (*(volatile int *)abort_flag) return false;
+        if ((it & 63) == 63 && now_ns() - t0 > limit_ns) {
+            latch_status(status, MORPH_ETIMEOUT);
+            atomicExch(abort_flag, 1);
+            return false;
+        }
+        __nanosleep(200);
+    }
+}
+
+// Packed tile variants reachable from the batch: stages {1, 2} x column
+// counters {none, 2-row register, 6 planes, 16 planes} x horizontal
+// {none, reach<=1, halo 1, 2, 4 words}.
+template <int NST, bool HS, int KMAX, int HALO, bool HX1>
+__device__ __noinline__ void tile_fn(const PackedArgs &a, int bx, int by, uint32_t *sm) {
+    packed_tile<NST, HS, KMAX, HALO, HX1>(a, bx, by, sm);
+}
+
+template <int NST, int KMAX>
+__device__ __forceinline__ void tile_h(int h, const PackedArgs &a, int bx, int by, uint32_t *sm) {
+    switch (h) {
+    case 0: tile_fn<NST, false, KMAX, 1, false>(a, bx, by, sm); break;
+    case 1: tile_fn<NST, true, KMAX, 1, true>(a, bx, by, sm); break;
+    case 2: tile_fn<NST, true, KMAX, 1, false>(a, bx, by, sm); break;
+    case 3: tile_fn<NST, true, KMAX, 2, false>(a, bx, by, sm); break;
+    default: tile_fn<NST, true, KMAX, 4, false>(a, bx, by, sm); break;
+    }
+}
+
+template <int NST>
+__device__ __forceinline__ void tile_k(int k, int h, const PackedArgs &a, int bx, int by, uint32_t *sm) {
+    switch (k) {
+    case 0: tile_h<NST, 0>(h, a, bx, by, sm); break;
+    case 1: tile_h<NST, 2>(h, a, bx, by, sm); break;
+    case 2: tile_h<NST, 6>(h, a, bx, by, sm); break;
+    default: tile_h<NST, 16>(h, a, bx, by, sm); break;
+    }
+}
+
+__device__ void run_packed_tile(int variant, const PackedArgs &a, int bx, int by, uint32_t *sm) {
+    const int h = variant % 5, k = (variant / 5) % 4, nst = variant / 20;
+    if (nst == 0) tile_k<1>(k, h, a, bx, by, sm);
+    else tile_k<2>(k, h, a, bx, by, sm);
+}
+
+template <int NWT, int KMAX>
+__device__ __noinline__ void vpass_fn(const VArgs &a, int bx, uint32_t *sm) {
+    vpass_tile<NWT, KMAX>(a, bx, sm);
+}
+
+__device__ void run_vpass(int vkind, const VArgs &a, int bx, uint32_t *sm) {
+    switch (vkind) {
+    case 0: vpass_fn<2, 3>(a, bx, sm); break;
+    case 1: vpass_fn<2, 6>(a, bx, sm); break;
+    case 2: vpass_fn<2, 16>(a, bx, sm); break;
+    case 3: vpass_fn<8, 3>(a, bx, sm); break;
+    case 4: vpass_fn<8, 6>(a, bx, sm); break;
+    default: vpass_fn<8, 16>(a, bx, sm); break;
+    }
+}
+
+struct Ctrl {
+    int head, abort_flag;
+    int pad[62];
+    // followed by int done[n_jobs][MAX_PH] and int overflow[n_jobs]
+};
+
+__global__ void __launch_bounds__(BATCH_THREADS, 2) k_batch(const uint8_t *plan, uint8_t *ws,
+                                                           int *status) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    __shared__ int s_item, s_ok;
+    const BatchHeader *hdr = reinterpret_cast<const BatchHeader *>(plan);
+    const BatchJob *jobs = reinterpret_cast<const BatchJob *>(plan + hdr->jobs_off);
+    const BatchItem *items = reinterpret_cast<const BatchItem *>(plan + hdr->items_off);
+    Ctrl *ctrl = reinterpret_cast<Ctrl *>(ws);
+    int *done = reinterpret_cast<int *>(ws + sizeof(Ctrl));
+    int *overflow = done + (size_t)hdr->n_jobs * MAX_PH;
+    const int n_items = hdr->n_items;
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_item = *(volatile int *)&ctrl->abort_flag ? n_items : atomicAdd(&ctrl->head, 1);
+        }
+        __syncthreads();
+        const int i = s_item;
+        if (i >= n_items) break;
+        const BatchItem it = items[i];
+        const BatchJob &J = jobs[it.job];
+        if (threadIdx.x == 0) {
+            bool ok = true;
+            if (it.phase > 0)
+                ok = wait_count(done + (size_t)it.job * MAX_PH + it.phase - 1,
+                                J.phase_items[it.phase - 1], &ctrl->abort_flag, status,
+                                (unsigned long long)hdr->wait_limit_ns);
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        __threadfence();
+
+        const bool ovf = it.phase > 0 && *(volatile int *)(overflow + it.job) != 0;
+        switch (it.kind) {
+        case IK_PACKED:
+            run_packed_tile(J.variant, J.pa, it.idx % J.gx, it.idx / J.gx, sm);
+            break;
+        case IK_B2R_COUNT: {
+            const int r0 = it.idx * RLE_ROWS_PER_ITEM;
+            b2r_count_rows(J.src, J.sstride, J.W, r0, min(J.H, r0 + RLE_ROWS_PER_ITEM),
+                           reinterpret_cast<int32_t *>(ws + J.off_counts));
+            break;
+        }
+        case IK_B2R_WRITE: {
+            if (ovf) break;
+            const int r0 = it.idx * RLE_ROWS_PER_ITEM;
+            b2r_write_rows(J.src, J.sstride, J.W, r0, min(J.H, r0 + RLE_ROWS_PER_ITEM),
+                           reinterpret_cast<const int32_t *>(ws + J.off_rpA),
+                           reinterpret_cast<uint16_t *>(ws + J.off_runsA));
+            break;
+        }
+        case IK_SCAN: {
+            if (ovf) break;
+            // output buffer of the phase that this scan completes
+            const int st = J.phase_stage[it.phase];
+            const bool toA = st < 0 || st == 1;
+            int32_t *rp = reinterpret_cast<int32_t *>(ws + (toA ? J.off_rpA : J.off_rpB));
+            int64_t *nr = reinterpret_cast<int64_t *>(ws + (toA ? J.off_nA : J.off_nB));
+            scan_rows_block(reinterpret_cast<const int32_t *>(ws + J.off_counts), J.H, rp, nr, J.cap,
+                            status);
+            if (threadIdx.x == 0 && rp[J.H] > J.cap) atomicExch(overflow + it.job, 1);
+            break;
+        }
+        case IK_ROW_COUNT:
+        case IK_ROW_WRITE: {
+            if (ovf) break;
+            const int st = J.phase_stage[it.phase];
+            const bool fromA = st == 0;
+            const RleIn in{reinterpret_cast<const int32_t *>(ws + (fromA ? J.off_rpA : J.off_rpB)),
+                           reinterpret_cast<const uint16_t *>(ws + (fromA ? J.off_runsA : J.off_runsB)),
+                           J.W, J.H};
+            const int r0 = it.idx * RLE_ROWS_PER_ITEM;
+            const bool write = it.kind == IK_ROW_WRITE;
+            rowpass_rows(in, J.rop[st], write, reinterpret_cast<int32_t *>(ws + J.off_counts),
+                         reinterpret_cast<const int32_t *>(ws + (fromA ? J.off_rpB : J.off_rpA)),
+                         reinterpret_cast<uint16_t *>(ws + (fromA ? J.off_runsB : J.off_runsA)), r0,
+                         min(J.H, r0 + RLE_ROWS_PER_ITEM));
+            break;
+        }
+        case IK_V_COUNT:
+        case IK_V_WRITE: {
+            if (ovf) break;
+            const int st = J.phase_stage[it.phase];
+            const bool fromA = st == 0;
+            VArgs va = J.va[st];
+            va.in.row_ptr = reinterpret_cast<const int32_t *>(ws + (fromA ? J.off_rpA : J.off_rpB));
+            va.in.runs = reinterpret_cast<const uint16_t *>(ws + (fromA ? J.off_runsA : J.off_runsB));
+            va.counts = reinterpret_cast<int32_t *>(ws + J.off_counts);
+            va.out_row_ptr = reinterpret_cast<const int32_t *>(ws + (fromA ? J.off_rpB : J.off_rpA));
+            va.out = reinterpret_cast<uint16_t *>(ws + (fromA ? J.off_runsB : J.off_runsA));
+            va.write = it.kind == IK_V_WRITE;
+            run_vpass(J.vkind[st], va, it.idx, sm);
+            break;
+        }
+        case IK_R2B: {
+            if (ovf) break;
+            const bool fromA = J.nst == 2;  // last stage wrote A (two stages) or B (one)
+            const RleIn in{reinterpret_cast<const int32_t *>(ws + (fromA ? J.off_rpA : J.off_rpB)),
+                           reinterpret_cast<const uint16_t *>(ws + (fromA ? J.off_runsA : J.off_runsB)),
+                           J.W, J.H};
+            const int r0 = it.idx * RLE_ROWS_PER_ITEM;
+            r2b_rows(in, J.dst, J.dstride, J.nw_cover, r0, min(J.H, r0 + RLE_ROWS_PER_ITEM), sm);
+            break;
+        }
+        default:
+            break;
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) atomicAdd(done + (size_t)it.job * MAX_PH + it.phase, 1);
+    }
+}
+
+// ------------------------------------------------------------ host side
+int bitlen(int v) {
+    int k = 0;
+    while (v) { ++k; v >>= 1; }
+    return k;
+}
+
+int packed_variant(const PackedArgs &a) {
+    const int kidx = [&] {
+        const int km = packed_kmax(a);
+        if (km == 0) return 0;
+        if (km == 2) return 1;
+        if (km <= 6) return 2;
+        return 3;
+    }();
+    int h;
+    if (!a.hmode) h = 0;
+    else if (a.sw <= 3 && a.ex[0] <= 1 && a.sw - 1 - a.ex[0] <= 1) h = 1;
+    else {
+        const int halo = packed_halo(a.sw, a.ex[0]);
+        h = halo == 1 ? 2 : (halo == 2 ? 3 : 4);
+    }
+    return ((a.nst - 1) * 4 + kidx) * 5 + h;
+}
+
+struct Clip {
+    int sw, sh, ox, oy;
+};
+Clip clip_rect(int W, int H, int sw, int sh, int ox, int oy) {
+    int l = ox, r = sw - 1 - ox, u = oy, d = sh - 1 - oy;
+    if (l > W - 1) l = W - 1;
+    if (r > W - 1) r = W - 1;
+    if (u > H - 1) u = H - 1;
+    if (d > H - 1) d = H - 1;
+    return {l + r + 1, u + d + 1, l, u};
+}
+
+morph_status berr(morph_status st, const char *msg, int job) {
+    set_error("job %d: %s", job, msg);
+    return st;
+}
+
+// Build jobs and items; returns MORPH_OK and fills the vectors.
+morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per_row,
+                   std::vector<BatchJob> &J, std::vector<BatchItem> &I, int64_t &ws_ctrl,
+                   int64_t &ws_total, int &smem) {
+    J.assign(n, BatchJob{});
+    smem = 0;
+    int64_t off = al(sizeof(Ctrl) + (size_t)n * MAX_PH * sizeof(int) + (size_t)n * sizeof(int));
+    ws_ctrl = off;
+    for (int j = 0; j < n; ++j) {
+        const morph_job &q = jobs[j];
+        BatchJob &b = J[j];
+        memset(&b, 0, sizeof(b));
+        const morph_image &s = q.src, &d = q.dst;
+        auto packed = [](const morph_image &m) { return m.fmt == MORPH_PACKED32 || m.fmt == MORPH_PACKED64; };
+        if (!packed(s) || !packed(d)) return berr(MORPH_EINVAL, "src and dst must be packed", j);
+        if (s.width < 1 || s.height < 1 || s.width != d.width || s.height != d.height)
+            return berr(MORPH_EINVAL, "bad or different sizes", j);
+        if (!s.words || !d.words || s.reserved || d.reserved) return berr(MORPH_EINVAL, "bad descriptor", j);
+        const int Bs = s.fmt == MORPH_PACKED32 ? 32 : 64, Bd = d.fmt == MORPH_PACKED32 ? 32 : 64;
+        if (s.stride_words < (s.width + Bs - 1) / Bs || d.stride_words < (d.width + Bd - 1) / Bd)
+            return berr(MORPH_EINVAL, "stride too small", j);
+        if ((uintptr_t)s.words % (Bs / 8) || (uintptr_t)d.words % (Bd / 8))
+            return berr(MORPH_EINVAL, "misaligned words", j);
+        if (q.op < MORPH_ERODE || q.op > MORPH_CLOSE) return berr(MORPH_EINVAL, "bad op", j);
+        if (q.se_w < 1 || q.se_h < 1 || q.se_w > 65535 || q.se_h > 65535 || q.origin_x < 0 ||
+            q.origin_x >= q.se_w || q.origin_y < 0 || q.origin_y >= q.se_h)
+            return berr(MORPH_EINVAL, "bad structuring element", j);
+        {
+            const uintptr_t slo = (uintptr_t)s.words, dlo = (uintptr_t)d.words;
+            const uintptr_t shi = slo + (uintptr_t)((int64_t)(s.height - 1) * s.stride_words * (Bs / 8) + (s.width + Bs - 1) / Bs * (Bs / 8));
+            const uintptr_t dhi = dlo + (uintptr_t)((int64_t)(d.height - 1) * d.stride_words * (Bd / 8) + (d.width + Bd - 1) / Bd * (Bd / 8));
+            if (slo < dhi && dlo < shi) return berr(MORPH_EINVAL, "dst overlaps src", j);
+        }
+        const int W = s.width, H = s.height;
+        const Clip c = clip_rect(W, H, q.se_w, q.se_h, q.origin_x, q.origin_y);
+        const int nw_cover = d.fmt == MORPH_PACKED32 ? (W + 31) / 32 : 2 * ((W + 63) / 64);
+        b.path = q.path;
+        if (q.path == MORPH_PATH_PACKED) {
+            PackedArgs &a = b.pa;
+            memset(&a, 0, sizeof(a));
+            a.src = (const uint32_t *)s.words;
+            a.sstride = s.stride_words * (Bs / 32);
+            a.dst = (uint32_t *)d.words;
+            a.dstride = d.stride_words * (Bd / 32);
+            a.W = W;
+            a.H = H;
+            a.nw_valid = (W + 31) / 32;
+            a.nw_cover = nw_cover;
+            if (packed_plan(a, q.op, c.sw, c.sh, c.ox, c.oy, tile_rows, MAX_THREADS) != 0)
+                return berr(MORPH_EINVAL, "rectangle reaches more than 128 pixels sideways", j);
+            b.variant = packed_variant(a);
+            const dim3 g = packed_grid(a);
+            b.gx = g.x;
+            b.nphase = 1;
+            b.phase_kind[0] = IK_PACKED;
+            b.phase_items[0] = g.x * g.y;
+            b.phase_stage[0] = -1;
+            const int sb = (int)packed_smem_bytes(a);
+            if (sb > smem) smem = sb;
+        } else if (q.path == MORPH_PATH_RLE) {
+            if (W > 65535) return berr(MORPH_EINVAL, "RLE path needs width <= 65535", j);
+            b.src = (const uint32_t *)s.words;
+            b.sstride = s.stride_words * (Bs / 32);
+            b.dst = (uint32_t *)d.words;
+            b.dstride = d.stride_words * (Bd / 32);
+            b.W = W;
+            b.H = H;
+            b.nw_cover = nw_cover;
+            b.nst = (q.op == MORPH_OPEN || q.op == MORPH_CLOSE) ? 2 : 1;
+            const int rpr = rle_runs_per_row > 0 ? rle_runs_per_row : W / 16 + 4;
+            b.cap = (int64_t)H * (rpr < (W + 1) / 2 ? rpr : (W + 1) / 2);
+            if (b.cap < 1) b.cap = 1;
+            b.off_counts = off; off += al((size_t)H * 4);
+            b.off_nA = off; off += al(8);
+            b.off_nB = off; off += al(8);
+            b.off_rpA = off; off += al((size_t)(H + 1) * 4);
+            b.off_rpB = off; off += al((size_t)(H + 1) * 4);
+            b.off_runsA = off; off += al((size_t)b.cap * 4);
+            b.off_runsB = off; off += al((size_t)b.cap * 4);
+            const int rows_items = (H + RLE_ROWS_PER_ITEM - 1) / RLE_ROWS_PER_ITEM;
+            int p = 0;
+            auto add = [&](int kind, int items, int stage) {
+                b.phase_kind[p] = kind;
+                b.phase_items[p] = items;
+                b.phase_stage[p] = stage;
+                ++p;
+            };
+            add(IK_B2R_COUNT, rows_items, -1);
+            add(IK_SCAN, 1, -1);
+            add(IK_B2R_WRITE, rows_items, -1);
+            for (int st = 0; st < b.nst; ++st) {
+                // stage order: open = erode then dilate; close = dilate then erode
+                const bool dil = (q.op == MORPH_DILATE) || (q.op == MORPH_OPEN && st == 1) ||
+                                 (q.op == MORPH_CLOSE && st == 0);
+                b.rop[st] = RowOp{dil ? 1 : 0, c.sw, c.ox, W};
+                if (c.sh == 1) {
+                    add(IK_ROW_COUNT, rows_items, st);
+                    add(IK_SCAN, 1, st);
+                    add(IK_ROW_WRITE, rows_items, st);
+                } else {
+                    VArgs &v = b.va[st];
+                    memset(&v, 0, sizeof(v));
+                    v.in.W = W;
+                    v.in.H = H;
+                    v.op = b.rop[st];
+                    v.inv = dil;
+                    v.sh = c.sh;
+                    v.ey = dil ? c.sh - 1 - c.oy : c.oy;
+                    v.K = bitlen(c.sh);
+                    for (int k = 0; k < 16; ++k) v.eqm[k] = ((c.sh >> k) & 1) ? 0u : ONES;
+                    vpass_plan(v, W, H, c.sh);
+                    v.capacity = b.cap;
+                    const int km = vpass_kmax(v.K);
+                    b.vkind[st] = (v.nwt == 2 ? 0 : 3) + (km == 3 ? 0 : (km == 6 ? 1 : 2));
+                    const int sb = (int)vpass_smem_bytes(v);
+                    if (sb > smem) smem = sb;
+                    add(IK_V_COUNT, vpass_grid(v), st);
+                    add(IK_SCAN, 1, st);
+                    add(IK_V_WRITE, vpass_grid(v), st);
+                }
+            }
+            add(IK_R2B, rows_items, -1);
+            b.nphase = p;
+            const int sb = 8 * nw_cover * 4;
+            if (sb > smem) smem = sb;
+        } else {
+            return berr(MORPH_EINVAL, "path must be MORPH_PATH_PACKED or MORPH_PATH_RLE", j);
+        }
+    }
+    ws_total = off;
+    // phase-major item order: every item of phase p of a job comes after all
+    // items of its phase p-1
+    I.clear();
+    int maxph = 0;
+    for (auto &b : J) maxph = b.nphase > maxph ? b.nphase : maxph;
+    for (int p = 0; p < maxph; ++p)
+        for (int j = 0; j < n; ++j)
+            if (p < J[j].nphase)
+                for (int k = 0; k < J[j].phase_items[p]; ++k)
+                    I.push_back(BatchItem{j, (int16_t)p, (int16_t)J[j].phase_kind[p], k});
+    return MORPH_OK;
+}
+
+}  // namespace
+}  // namespace morph
+
+using namespace morph;
+
+extern "C" {
+
+size_t morph_batch_plan_bytes(const morph_job *jobs, int n_jobs, int tile_rows,
+                              int rle_runs_per_row) {
+    if (!jobs || n_jobs < 1) return 0;
+    std::vector<BatchJob> J;
+    std::vector<BatchItem> I;
+    int64_t c, t;
+    int smem;
+    if (build(jobs, n_jobs, tile_rows, rle_runs_per_row, J, I, c, t, smem) != MORPH_OK) return 0;
+    return al(sizeof(BatchHeader)) + al(J.size() * sizeof(BatchJob)) + al(I.size() * sizeof(BatchItem));
+}
+
+morph_status morph_batch_plan_build(void *host_plan, size_t plan_bytes, const morph_job *jobs,
+                                    int n_jobs, int tile_rows, int rle_runs_per_row) {
+    if (!host_plan || !jobs || n_jobs < 1) {
+        set_error("NULL plan or jobs, or n_jobs < 1");
+        return MORPH_EINVAL;
+    }
+    std::vector<BatchJob> J;
+    std::vector<BatchItem> I;
+    int64_t ctrl, total;
+    int smem;
+    morph_status st = build(jobs, n_jobs, tile_rows, rle_runs_per_row, J, I, ctrl, total, smem);
+    if (st != MORPH_OK) return st;
+    BatchHeader h;
+    memset(&h, 0, sizeof(h));
+    h.magic = PLAN_MAGIC;
+    h.n_jobs = n_jobs;
+    h.n_items = (int32_t)I.size();
+    h.smem_bytes = smem;
+    h.jobs_off = (int64_t)al(sizeof(BatchHeader));
+    h.items_off = h.jobs_off + (int64_t)al(J.size() * sizeof(BatchJob));
+    h.plan_bytes = h.items_off + (int64_t)al(I.size() * sizeof(BatchItem));
+    h.ws_ctrl_bytes = ctrl;
+    h.ws_bytes = total;
+    h.wait_limit_ns = WAIT_LIMIT_NS;
+    if ((int64_t)plan_bytes < h.plan_bytes) {
+        set_error("plan buffer of %zu bytes < %lld needed", plan_bytes, (long long)h.plan_bytes);
+        return MORPH_ENOMEM;
+    }
+    uint8_t *p = (uint8_t *)host_plan;
+    memset(p, 0, (size_t)h.plan_bytes);
+    memcpy(p, &h, sizeof(h));
+    memcpy(p + h.jobs_off, J.data(), J.size() * sizeof(BatchJob));
+    memcpy(p + h.items_off, I.data(), I.size() * sizeof(BatchItem));
+    return MORPH_OK;
+}
+
+size_t morph_batch_workspace_size(const void *host_plan) {
+    const BatchHeader *h = (const BatchHeader *)host_plan;
+    if (!h || h->magic != PLAN_MAGIC) return 0;
+    return (size_t)h->ws_bytes;
+}
+
+morph_status morph_batch_plan_debug(void *host_plan, int what, long long value) {
+    BatchHeader *h = (BatchHeader *)host_plan;
+    if (!h || h->magic != PLAN_MAGIC) {
+        set_error("NULL or invalid plan");
+        return MORPH_EINVAL;
+    }
+    if (what == 0) {
+        if (value < 1000000) value = 1000000;
+        h->wait_limit_ns = value;
+        return MORPH_OK;
+    }
+    if (what == 1) {
+        BatchJob *J = (BatchJob *)((uint8_t *)host_plan + h->jobs_off);
+        for (int j = 0; j < h->n_jobs; ++j)
+            if (J[j].nphase > 1) {
+                J[j].phase_items[0] += (int32_t)value;
+                return MORPH_OK;
+            }
+        set_error("no job with more than one phase");
+        return MORPH_EINVAL;
+    }
+    set_error("unknown debug request %d", what);
+    return MORPH_EINVAL;
+}
+
+int morph_batch_items(const void *host_plan) {
+    const BatchHeader *h = (const BatchHeader *)host_plan;
+    if (!h || h->magic != PLAN_MAGIC) return -1;
+    return h->n_items;
+}
+
+morph_status morph_batch_launch(const void *dev_plan, const void *host_plan, void *workspace,
+                                size_t workspace_bytes, int n_ctas, void *stream) {
+    const BatchHeader *h = (const BatchHeader *)host_plan;
+    if (!dev_plan || !h || h->magic != PLAN_MAGIC) {
+        set_error("NULL or invalid plan");
+        return MORPH_EINVAL;
+    }
+    if (!workspace || (int64_t)workspace_bytes < h->ws_bytes) {
+        set_error("workspace of %zu bytes < %lld needed", workspace ? workspace_bytes : (size_t)0,
+                  (long long)h->ws_bytes);
+        return MORPH_ENOMEM;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int smem = h->smem_bytes;
+    cudaError_t e = cudaSuccess;
+    if (smem > 48 * 1024) e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess && n_ctas <= 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, BATCH_THREADS, smem);
+        n_ctas = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(workspace, 0, (size_t)h->ws_ctrl_bytes, s);
+    if (e == cudaSuccess) {
+        k_batch<<<n_ctas, BATCH_THREADS, smem, s>>>((const uint8_t *)dev_plan, (uint8_t *)workspace,
+                                                    device_status_ptr());
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        set_error("batch launch: %s", cudaGetErrorString(e));
+        return MORPH_ECUDA;
+    }
+    return MORPH_OK;
+}
+
+}  // extern "C"

@@ -13,6 +13,9 @@ namespace morph {
 constexpr uint32_t ONES = 0xFFFFFFFFu;
 constexpr int MAX_THREADS = 256;   // CTA size of the tile kernels
 
+// Message for morph_last_error() (printf-style), see abi.cu.
+void set_error(const char *fmt, ...);
+
 // Device-side status latch (first non-OK code wins), see abi.cu.
 int *device_status_ptr();          // host: address of the status word on the current device
 
@@ -70,12 +73,17 @@ struct PackedArgs {
     int halo_words;       // extra computed words on each side of a strip
     int nstrips;
     int slot_words;       // smem words per group row slot
+    int vec;              // 64-bit loads / stores allowed (aligned bases, even strides)
 };
 
-int packed_halo(int sw, int ex);   // smem / register halo words of the H stage
-cudaError_t launch_packed(PackedArgs &a, cudaStream_t s, int band_rows_hint);
+int packed_halo(int sw, int ex);   // register-window halo words of the H stage (0: too wide)
 int packed_plan(PackedArgs &a, int op, int sw, int sh, int ox, int oy, int band_rows_hint,
                 int block_threads_hint);
+size_t packed_smem_bytes(const PackedArgs &a);
+int packed_kmax(const PackedArgs &a);
+int packed_threads(const PackedArgs &a);
+dim3 packed_grid(const PackedArgs &a);
+cudaError_t launch_packed(PackedArgs &a, cudaStream_t s);
 
 // ----------------------------------------------------------------- RLE ---
 struct RleIn {             // read-only view of an RLE image
@@ -90,6 +98,39 @@ struct RleOut {
     int64_t capacity;
     int64_t *n_runs;
 };
+
+// Within-line run pass: erosion (dilate = 0, o = erosion origin) or dilation
+// (dilate = 1, o = dilation origin) of every run by a width-sw segment.
+struct RowOp {
+    int dilate, sw, o, W;
+};
+
+// Between-line pass over an RLE image (see rle_tile.cuh).
+struct VArgs {
+    RleIn in;
+    RowOp op;
+    int inv;                 // complement before and after (dilation)
+    int sh, ey, K;
+    uint32_t eqm[16];
+    int nw_ext;              // words covering positions 0..W
+    int nwt;                 // words per thread (2 or 8)
+    int tpr, groups, band, rb, slot_words;
+    int write;
+    int32_t *counts;
+    const int32_t *out_row_ptr;
+    int64_t capacity;
+    uint16_t *out;
+};
+
+// Fill the tiling of the between-line pass for an image of width W, height
+// H and window height sh (block size up to MAX_THREADS).
+void vpass_plan(VArgs &a, int W, int H, int sh);
+size_t vpass_smem_bytes(const VArgs &a);
+int vpass_threads(const VArgs &a);
+int vpass_grid(const VArgs &a);
+int vpass_kmax(int K);
+// rows handled by one work item of the row-wise RLE kernels
+constexpr int RLE_ROWS_PER_ITEM = 64;
 
 cudaError_t launch_rle_from_bitmap(const uint32_t *src, int64_t sstride, int W, int H,
                                    RleOut out, int32_t *counts, int *status, cudaStream_t s);

@@ -1,0 +1,389 @@
+// Device bodies of the run-length kernels, written over explicit row ranges
+// (or band indices) so that both the single-image launches and the
+// persistent batch kernel run them.
+//
+// RLE image: row_ptr[H+1] and uint16 runs (start, end) with end exclusive
+// (section "Run Length Image Coding").  Seen as a uint16 array, the runs of a
+// row are exactly the ascending list of its transitions (0->1 at a start,
+// 1->0 at an end); the kernels read and write them that way — the paper's
+// TransitionSource / TransitionSink abstraction (section "Between Line
+// Boolean Operations") in array form.  Variable-size outputs go through
+// count -> exclusive prefix sum over rows -> write.
+#pragma once
+
+#include "morph_internal.cuh"
+
+namespace morph {
+
+constexpr unsigned FULL_MASK = 0xFFFFFFFFu;
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ int warp_excl_scan(int v, int lane, int &total) {
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL_MASK, x, o);
+        if (lane >= o) x += y;
+    }
+    total = __shfl_sync(FULL_MASK, x, 31);
+    return x - v;
+}
+
+// Word k of a packed row with padding bits cleared; 0 outside the row.
+__device__ __forceinline__ uint32_t row_word(const uint32_t *row, int k, int nw_valid, int W) {
+    return (k >= 0 && k < nw_valid) ? (__ldg(row + k) & word_mask(k, W)) : 0u;
+}
+
+// ------------------------------------------------------ bitmap -> RLE (K6)
+// Transition word k: bit b set iff pixel 32k+b differs from pixel 32k+b-1
+// (pixel -1 and pixels >= W are 0).  Words 0 .. W/32 cover positions 0..W.
+// One warp per row; rows [r0, r1).
+__device__ __forceinline__ void b2r_count_rows(const uint32_t *src, int64_t sstride, int W, int r0,
+                                               int r1, int32_t *counts) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int nw_valid = (W + 31) >> 5, nw_ext = (W >> 5) + 1;
+    for (int y = r0 + warp; y < r1; y += nwarps) {
+        const uint32_t *row = src + (int64_t)y * sstride;
+        int cnt = 0;
+        for (int k = lane; k < nw_ext; k += 32) {
+            const uint32_t w = row_word(row, k, nw_valid, W);
+            const uint32_t p = row_word(row, k - 1, nw_valid, W);
+            cnt += __popc(w ^ ((w << 1) | (p >> 31)));
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(FULL_MASK, cnt, o);
+        if (lane == 0) counts[y] = cnt >> 1;
+    }
+}
+
+__device__ __forceinline__ void b2r_write_rows(const uint32_t *src, int64_t sstride, int W, int r0,
+                                               int r1, const int32_t *row_ptr, uint16_t *runs) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int nw_valid = (W + 31) >> 5, nw_ext = (W >> 5) + 1;
+    for (int y = r0 + warp; y < r1; y += nwarps) {
+        const uint32_t *row = src + (int64_t)y * sstride;
+        int64_t pos0 = 2 * (int64_t)row_ptr[y];
+        for (int k0 = 0; k0 < nw_ext; k0 += 32) {
+            const int k = k0 + lane;
+            uint32_t t = 0;
+            if (k < nw_ext) {
+                const uint32_t w = row_word(row, k, nw_valid, W);
+                const uint32_t p = row_word(row, k - 1, nw_valid, W);
+                t = w ^ ((w << 1) | (p >> 31));
+            }
+            int tot;
+            const int ex = warp_excl_scan(__popc(t), lane, tot);
+            int64_t pos = pos0 + ex;
+            while (t) {
+                const int b = __ffs(t) - 1;
+                runs[pos++] = (uint16_t)(32 * k + b);
+                t &= t - 1;
+            }
+            pos0 += tot;
+        }
+    }
+}
+
+// Exclusive prefix sum of counts[0..H) into row_ptr[0..H], the total into
+// row_ptr[H] and *n_runs; latches MORPH_ECAPACITY when total > capacity.
+// One CTA (any size that is a multiple of 32, up to 1024).
+__device__ __forceinline__ void scan_rows_block(const int32_t *counts, int H, int32_t *row_ptr,
+                                                int64_t *n_runs, int64_t capacity, int *status) {
+    constexpr int ITEMS = 4;
+    __shared__ int64_t wsum[32];
+    __shared__ int64_t base_s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int nthreads = blockDim.x;
+    if (tid == 0) base_s = 0;
+    __syncthreads();
+    for (int start = 0; start < H; start += nthreads * ITEMS) {
+        int64_t v[ITEMS], loc = 0;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            const int idx = start + tid * ITEMS + j;
+            v[j] = idx < H ? counts[idx] : 0;
+            loc += v[j];
+        }
+        int64_t x = loc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(FULL_MASK, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int64_t s = lane < nwarps ? wsum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t y = __shfl_up_sync(FULL_MASK, s, o);
+                if (lane >= o) s += y;
+            }
+            wsum[lane] = s;  // inclusive over warps
+        }
+        __syncthreads();
+        const int64_t base = base_s;
+        int64_t run = base + (warp ? wsum[warp - 1] : 0) + x - loc;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            const int idx = start + tid * ITEMS + j;
+            if (idx < H) row_ptr[idx] = (int32_t)run;
+            run += v[j];
+        }
+        __syncthreads();
+        if (tid == 0) base_s = base + wsum[nwarps - 1];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const int64_t total = base_s;
+        row_ptr[H] = (int32_t)total;
+        if (n_runs) *n_runs = total;
+        if (total > capacity) latch_status(status, MORPH_ECAPACITY);
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------ RLE -> bitmap (K7)
+// Each run XORs its two transition bits into a per-warp row buffer in shared
+// memory; a prefix XOR across the row (within words, then a ballot parity
+// scan across words) turns transitions back into pixels.  sm: nwarps *
+// nw_cover words.
+__device__ __forceinline__ void r2b_rows(const RleIn &in, uint32_t *dst, int64_t dstride,
+                                         int nw_cover, int r0, int r1, uint32_t *sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    uint32_t *buf = sm + (size_t)warp * nw_cover;
+    const int nbits = 32 * nw_cover;
+    for (int y = r0 + warp; y < r1; y += nwarps) {
+        for (int k = lane; k < nw_cover; k += 32) buf[k] = 0;
+        __syncwarp();
+        const int a = in.row_ptr[y], b = in.row_ptr[y + 1];
+        for (int i = a + lane; i < b; i += 32) {
+            const int s = in.runs[2 * (int64_t)i], e = in.runs[2 * (int64_t)i + 1];
+            if (s < nbits) atomicXor(buf + (s >> 5), 1u << (s & 31));
+            if (e < nbits) atomicXor(buf + (e >> 5), 1u << (e & 31));
+        }
+        __syncwarp();
+        uint32_t carry = 0;
+        for (int k0 = 0; k0 < nw_cover; k0 += 32) {
+            const int k = k0 + lane;
+            const uint32_t T = k < nw_cover ? buf[k] : 0u;
+            const unsigned bal = __ballot_sync(FULL_MASK, __popc(T) & 1);
+            const uint32_t pre = (__popc(bal & lanemask_lt()) & 1) ^ carry;
+            const uint32_t bits = prefix_xor(T) ^ (pre ? ONES : 0u);
+            if (k < nw_cover) dst[(int64_t)y * dstride + k] = bits & word_mask(k, in.W);
+            carry ^= __popc(bal) & 1;
+        }
+        __syncwarp();
+    }
+}
+
+// --------------------------------------------------- within-line pass (K4)
+// 1D erosion of a run [s, e) by a width-sw segment with origin ex (clipped
+// window): [s + ex, e - (sw-1-ex)), except that a run touching the left
+// (right) border keeps that end; dropped when empty.  1D dilation: every run
+// grows to [s - ox, e + sw-1-ox) clipped to [0, W); consecutive grown runs
+// overlap or touch exactly when the gap between the original runs is
+// <= sw - 1, and then merge (their inner transitions are dropped).  This is
+// the paper's erode1d / dilate1d (section "Within-Line Morphological
+// Operations") with the shrink amounts of the rectangle's origin.
+struct RunT {
+    int s, e;      // transformed run
+    bool ks, ke;   // keep its start / end transition
+};
+
+__device__ __forceinline__ RunT row_op(const uint16_t *runs, int64_t i, int64_t a, int64_t b,
+                                       const RowOp &op) {
+    RunT r;
+    const int s = runs[2 * i], e = runs[2 * i + 1];
+    if (!op.dilate) {
+        r.s = (s == 0) ? 0 : s + op.o;
+        r.e = (e >= op.W) ? op.W : e - (op.sw - 1 - op.o);
+        r.ks = r.ke = r.s < r.e;
+    } else {
+        r.s = s - op.o < 0 ? 0 : s - op.o;
+        r.e = e + op.sw - 1 - op.o > op.W ? op.W : e + op.sw - 1 - op.o;
+        r.ks = (i == a) || (s - (int)runs[2 * i - 1] > op.sw - 1);
+        r.ke = (i == b - 1) || ((int)runs[2 * i + 2] - e > op.sw - 1);
+    }
+    return r;
+}
+
+// One warp per row; rows [r0, r1).  Count pass (write == 0) or write pass.
+__device__ __forceinline__ void rowpass_rows(const RleIn &in, const RowOp &op, int write,
+                                             int32_t *counts, const int32_t *out_row_ptr,
+                                             uint16_t *out, int r0, int r1) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int y = r0 + warp; y < r1; y += nwarps) {
+        const int64_t a = in.row_ptr[y], b = in.row_ptr[y + 1];
+        int64_t grp = write ? (int64_t)out_row_ptr[y] : 0;  // run index of the next output
+        int cnt = 0;
+        for (int64_t i0 = a; i0 < b; i0 += 32) {
+            const int64_t i = i0 + lane;
+            RunT r = {0, 0, false, false};
+            if (i < b) r = row_op(in.runs, i, a, b, op);
+            const unsigned bs = __ballot_sync(FULL_MASK, r.ks);
+            if (write) {
+                // group index of run i = number of kept starts up to i, minus one
+                const int incl = __popc(bs & (lanemask_lt() | (1u << lane)));
+                const int64_t gi = grp + incl - 1;
+                if (r.ks) out[2 * gi] = (uint16_t)r.s;
+                if (r.ke) out[2 * gi + 1] = (uint16_t)r.e;
+            }
+            grp += __popc(bs);
+            cnt += __popc(bs);
+        }
+        if (!write && lane == 0) counts[y] = cnt;
+    }
+}
+
+// --------------------------------------------------- between-line pass (K5)
+// Vertical erosion of the row-pass result by an sh-row window [y-ey, y-ey+sh-1]
+// (dilation: the same on the complement).  A tile owns `groups` bands of rows
+// across the full width; each thread owns NWT 32-pixel words of every row.
+// Per chunk of rb rows:
+//   P1 clear the transition slots; P2 every run of an input row (after the
+//   row pass) XORs its kept transitions into the slot; P3 one warp per slot
+//   turns transitions into pixels (prefix XOR); P4 every thread pushes its
+//   words into bit-sliced counters of consecutive covered rows — the "count
+//   reached sh" plane is the output row, i.e. the intersection of the sh
+//   neighbouring rows' intervals; P5 one warp per output row finds its
+//   transitions and counts them (count pass) or writes them at row_ptr
+//   (write pass).  sm: 2 * rb * groups * slot_words words.
+template <int NWT, int KMAX>
+__device__ __forceinline__ void vpass_tile(const VArgs &a, int bx, uint32_t *sm) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int g = tid / a.tpr, lt = tid - g * a.tpr;
+    const bool act = g < a.groups;
+    const int W = a.in.W, H = a.in.H;
+    const int nw_valid = (W + 31) >> 5;
+    const int slot = a.slot_words, nslot = a.rb * a.groups;
+    uint32_t *T = sm;                          // [rb][groups][slot]
+    uint32_t *O = sm + (size_t)nslot * slot;   // [rb][groups][slot]
+    const int Ybase = bx * a.groups * a.band;
+    const int iters = a.band + a.sh - 1;
+
+    uint32_t vmask[NWT], c[NWT][KMAX], sat[NWT];
+#pragma unroll
+    for (int t = 0; t < NWT; ++t) {
+        const int w = lt * NWT + t;
+        vmask[t] = (act && w < nw_valid) ? word_mask(w, W) : 0u;
+        sat[t] = 0;
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) c[t][k] = 0;
+    }
+
+    for (int c0 = 0; c0 < iters; c0 += a.rb) {
+        // P1: clear transition slots
+        for (int q = tid; q < nslot * slot; q += blockDim.x) T[q] = 0;
+        __syncthreads();
+        // P2: kept transitions of every input row of the chunk
+        for (int q = 0; q < nslot; ++q) {
+            const int i = q / a.groups, gq = q - i * a.groups;
+            if (gq != g || !act) continue;
+            const int r = Ybase + gq * a.band - a.ey + c0 + i;
+            if (r < 0 || r >= H) continue;
+            const int64_t ra = a.in.row_ptr[r], rb_ = a.in.row_ptr[r + 1];
+            uint32_t *slotp = T + (size_t)q * slot;
+            const int nbits = 32 * slot;
+            for (int64_t j = ra + lt; j < rb_; j += a.tpr) {
+                const RunT rt = row_op(a.in.runs, j, ra, rb_, a.op);
+                // the bounds guards only matter for a non-canonical input list
+                if (rt.ks && rt.s >= 0 && rt.s < nbits) atomicXor(slotp + (rt.s >> 5), 1u << (rt.s & 31));
+                if (rt.ke && rt.e >= 0 && rt.e < nbits) atomicXor(slotp + (rt.e >> 5), 1u << (rt.e & 31));
+            }
+        }
+        __syncthreads();
+        // P3: transitions -> pixels, one warp per slot row
+        for (int q = warp; q < nslot; q += nwarps) {
+            uint32_t *slotp = T + (size_t)q * slot;
+            uint32_t carry = 0;
+            for (int k0 = 0; k0 < a.nw_ext; k0 += 32) {
+                const int k = k0 + lane;
+                const uint32_t x = k < a.nw_ext ? slotp[k] : 0u;
+                const unsigned bal = __ballot_sync(FULL_MASK, __popc(x) & 1);
+                const uint32_t pre = (__popc(bal & lanemask_lt()) & 1) ^ carry;
+                if (k < a.nw_ext) slotp[k] = prefix_xor(x) ^ (pre ? ONES : 0u);
+                carry ^= __popc(bal) & 1;
+            }
+        }
+        __syncthreads();
+        // P4: column counters -> output rows
+        if (act) {
+            for (int i = 0; i < a.rb; ++i) {
+                const int r = Ybase + g * a.band - a.ey + c0 + i;
+                const bool rin = r >= 0 && r < H;
+                const uint32_t *tp = T + (size_t)(i * a.groups + g) * slot + lt * NWT;
+                uint32_t *op = O + (size_t)(i * a.groups + g) * slot + lt * NWT;
+#pragma unroll
+                for (int t = 0; t < NWT; ++t) {
+                    uint32_t v = ONES;
+                    if (rin) {
+                        const uint32_t x = tp[t];
+                        v = (a.inv ? ~x : x) | ~vmask[t];
+                    }
+                    uint32_t carry = v, eq = ONES;
+#pragma unroll
+                    for (int k = 0; k < KMAX; ++k) {
+                        if (k < a.K) {
+                            const uint32_t ck = c[t][k];
+                            const uint32_t nk = (ck ^ carry) & v;
+                            carry = ck & carry;
+                            c[t][k] = nk;
+                            eq &= nk ^ a.eqm[k];
+                        }
+                    }
+                    sat[t] = v & (sat[t] | eq);
+                    op[t] = (a.inv ? ~sat[t] : sat[t]) & vmask[t];
+                }
+            }
+        }
+        __syncthreads();
+        // P5: encode output rows
+        for (int q = warp; q < nslot; q += nwarps) {
+            const int i = q / a.groups, gq = q - i * a.groups;
+            const int it = c0 + i;
+            const int y0 = Ybase + gq * a.band;
+            const int y = y0 + it - (a.sh - 1);
+            if (it < a.sh - 1 || y >= y0 + a.band || y >= H) continue;
+            const uint32_t *op = O + (size_t)q * slot;
+            int64_t pos0 = a.write ? 2 * (int64_t)a.out_row_ptr[y] : 0;
+            int cnt = 0;
+            for (int k0 = 0; k0 < a.nw_ext; k0 += 32) {
+                const int k = k0 + lane;
+                uint32_t t = 0;
+                if (k < a.nw_ext) {
+                    const uint32_t w = op[k];
+                    const uint32_t p = k > 0 ? op[k - 1] : 0u;
+                    t = w ^ ((w << 1) | (p >> 31));
+                }
+                if (a.write) {
+                    int tot;
+                    const int ex = warp_excl_scan(__popc(t), lane, tot);
+                    int64_t pos = pos0 + ex;
+                    while (t) {
+                        const int b = __ffs(t) - 1;
+                        a.out[pos++] = (uint16_t)(32 * k + b);
+                        t &= t - 1;
+                    }
+                    pos0 += tot;
+                } else {
+                    cnt += __popc(t);
+                }
+            }
+            if (!a.write) {
+#pragma unroll
+                for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(FULL_MASK, cnt, o);
+                if (lane == 0) a.counts[y] = cnt >> 1;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+}  // namespace morph

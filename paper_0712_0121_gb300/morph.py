@@ -51,6 +51,19 @@ class morph_image(ctypes.Structure):
     ]
 
 
+class morph_job(ctypes.Structure):
+    _fields_ = [
+        ("op", ctypes.c_int32),
+        ("path", ctypes.c_int32),
+        ("se_w", ctypes.c_int32),
+        ("se_h", ctypes.c_int32),
+        ("origin_x", ctypes.c_int32),
+        ("origin_y", ctypes.c_int32),
+        ("src", morph_image),
+        ("dst", morph_image),
+    ]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError("libmorph.so is not built (run __graft_entry__.build() or "
@@ -80,6 +93,19 @@ def _load():
     lib.morph_status_string.restype = ctypes.c_char_p
     lib.morph_abi_version.argtypes = []
     lib.morph_abi_version.restype = ci
+    job_p = ctypes.POINTER(morph_job)
+    lib.morph_batch_plan_bytes.argtypes = [job_p, ci, ci, ci]
+    lib.morph_batch_plan_bytes.restype = sz
+    lib.morph_batch_plan_build.argtypes = [vp, sz, job_p, ci, ci, ci]
+    lib.morph_batch_plan_build.restype = ci
+    lib.morph_batch_workspace_size.argtypes = [vp]
+    lib.morph_batch_workspace_size.restype = sz
+    lib.morph_batch_items.argtypes = [vp]
+    lib.morph_batch_items.restype = ci
+    lib.morph_batch_plan_debug.argtypes = [vp, ci, ctypes.c_longlong]
+    lib.morph_batch_plan_debug.restype = ci
+    lib.morph_batch_launch.argtypes = [vp, vp, vp, sz, ci, vp]
+    lib.morph_batch_launch.restype = ci
     return lib
 
 
@@ -284,3 +310,62 @@ def sync_status(stream=None) -> int:
 
 def abi_version() -> int:
     return int(_lib.morph_abi_version())
+
+
+# ----------------------------------------------------------------- batch
+
+class Batch:
+    """A persistent batch launch over many packed pages (``morph_batch_*``).
+
+    ``jobs``: list of dicts with keys ``op`` ("erode"/"dilate"/"open"/"close"
+    or code), ``se`` ((se_w, se_h)), optional ``origin`` ((ox, oy), default
+    centre), ``path`` ("packed" or "rle"), ``src`` and ``dst`` (:class:`Packed`).
+    The plan is built on the host, copied to the device once, and every
+    :meth:`launch` is one kernel launch (graph-capturable)."""
+
+    def __init__(self, jobs, tile_rows: int = 0, rle_runs_per_row: int = 0, device="cuda",
+                 debug=None):
+        n = len(jobs)
+        if n < 1:
+            raise ValueError("empty batch")
+        arr = (morph_job * n)()
+        self._keep = []
+        for k, j in enumerate(jobs):
+            sw, sh = j["se"]
+            ox, oy = j.get("origin") or (sw // 2, sh // 2)
+            path = j.get("path", "packed")
+            arr[k].op = OPS.get(j["op"], j["op"])
+            arr[k].path = PATH_RLE if path in ("rle", PATH_RLE) else PATH_PACKED
+            arr[k].se_w, arr[k].se_h, arr[k].origin_x, arr[k].origin_y = sw, sh, ox, oy
+            arr[k].src = j["src"].desc()
+            arr[k].dst = j["dst"].desc()
+            self._keep.append((j["src"], j["dst"]))
+        nbytes = int(_lib.morph_batch_plan_bytes(arr, n, tile_rows, rle_runs_per_row))
+        if nbytes == 0:
+            # rebuild into a 1-byte buffer to get the reason
+            _check(_lib.morph_batch_plan_build(None, 0, arr, n, tile_rows, rle_runs_per_row))
+            raise MorphError(MORPH_EINVAL, "batch plan rejected")
+        self.host_plan = np.zeros(nbytes, dtype=np.uint8)
+        hp = self.host_plan.ctypes.data
+        _check(_lib.morph_batch_plan_build(hp, nbytes, arr, n, tile_rows, rle_runs_per_row))
+        for what, value in (debug or []):
+            _check(_lib.morph_batch_plan_debug(hp, what, value))
+        self.dev_plan = torch.from_numpy(self.host_plan).to(device)
+        self.ws_bytes = int(_lib.morph_batch_workspace_size(hp))
+        self.workspace = torch.empty(max(self.ws_bytes, 1), dtype=torch.uint8, device=device)
+        self.n_items = int(_lib.morph_batch_items(hp))
+        self.n_jobs = n
+
+    def launch(self, stream=None, n_ctas: int = 0) -> None:
+        _check(_lib.morph_batch_launch(self.dev_plan.data_ptr(), self.host_plan.ctypes.data,
+                                       self.workspace.data_ptr(), self.ws_bytes, n_ctas,
+                                       _stream_handle(stream)))
+
+    def capture(self, n_ctas: int = 0) -> "torch.cuda.CUDAGraph":
+        """Capture one launch in a CUDA graph (replay with ``g.replay()``)."""
+        self.launch(n_ctas=n_ctas)  # warm-up outside the capture (sets kernel attributes)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.launch(n_ctas=n_ctas)
+        return g

@@ -1,0 +1,117 @@
+"""The persistent batch launch: mixed page sizes, operations, rectangles and
+paths in one launch, each page bit-exact against the oracle, the same alone
+and in the mix, replayable from a CUDA graph; overflow and time-out reported
+through the device status without harming the context."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_0712_0121_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+M = pytest.importorskip("paper_0712_0121_gb300.morph")
+from gpu_helpers import NCORES, unpack_words  # noqa: E402
+
+
+def make_jobs(specs):
+    jobs, imgs = [], []
+    for k, (W, H, op, se, path, dens) in enumerate(specs):
+        img = synth.text_page(W, H, 9000 + k, dens, glyph=(4, 12, 6, 14), gap=(2, 6), ncols=2)[0]
+        src = M.pack(img, 64 if k % 3 else 32)
+        dst = M.Packed.empty(W, H, 32 if k % 2 else 64)
+        dst.words.fill_(-1)
+        jobs.append(dict(op=op, se=se, path=path, src=src, dst=dst))
+        imgs.append(img)
+    return jobs, imgs
+
+
+SPECS = [
+    (300, 200, "erode", (3, 3), "packed", 0.2),
+    (301, 177, "dilate", (5, 5), "rle", 0.1),
+    (517, 333, "open", (9, 9), "packed", 0.25),
+    (517, 333, "close", (9, 9), "rle", 0.25),
+    (1000, 50, "open", (41, 1), "rle", 0.15),
+    (1000, 50, "close", (1, 41), "packed", 0.15),
+    (77, 640, "dilate", (101, 1), "packed", 0.05),
+    (77, 640, "erode", (1, 31), "rle", 0.4),
+    (200, 120, "close", (15, 15), "rle", 0.02),
+    (200, 120, "open", (31, 31), "packed", 0.3),
+    (64, 64, "erode", (1, 1), "rle", 0.5),
+    (2550, 400, "close", (51, 51), "packed", 0.08),
+]
+
+
+def check_all(jobs, imgs):
+    for k, (j, img) in enumerate(zip(jobs, imgs)):
+        sw, sh = j["se"]
+        ref = oracle.apply(j["op"], img, sw, sh, mode="separable", threads=NCORES)
+        got = unpack_words(j["dst"].words, img.shape[1])
+        assert np.array_equal(got, ref), "job %d %s %s %s" % (k, j["op"], j["se"], j["path"])
+
+
+def test_mixed_batch_matches_oracle():
+    jobs, imgs = make_jobs(SPECS)
+    b = M.Batch(jobs)
+    b.launch()
+    assert M.sync_status() == M.MORPH_OK
+    check_all(jobs, imgs)
+
+
+def test_alone_equals_in_the_mix_and_graph_replay():
+    jobs, imgs = make_jobs(SPECS)
+    b = M.Batch(jobs)
+    g = b.capture()
+    for j in jobs:
+        j["dst"].words.fill_(0)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    assert M.sync_status() == M.MORPH_OK
+    check_all(jobs, imgs)
+    mixed = [j["dst"].words.clone() for j in jobs]
+    for k, j in enumerate(jobs):
+        alone = M.Packed.empty(j["dst"].width, j["dst"].height, j["dst"].word_bits)
+        one = M.Batch([dict(j, dst=alone)])
+        one.launch()
+        assert torch.equal(alone.words, mixed[k]), "job %d differs alone" % k
+        single = M.Packed.empty(j["dst"].width, j["dst"].height, j["dst"].word_bits)
+        M.morph_rect(j["op"], single, j["src"], *j["se"])
+        assert torch.equal(single.words, mixed[k]), "job %d differs from the single-op launch" % k
+
+
+def test_rle_buffer_overflow_is_reported_and_packed_jobs_survive():
+    specs = [(400, 100, "open", (3, 3), "rle", 0.5), (400, 100, "open", (3, 3), "packed", 0.5)]
+    jobs, imgs = make_jobs(specs)
+    b = M.Batch(jobs, rle_runs_per_row=2)
+    b.launch()
+    assert M.sync_status() == M.MORPH_ECAPACITY
+    ref = oracle.opening(imgs[1], 3, 3)
+    assert np.array_equal(unpack_words(jobs[1]["dst"].words, 400), ref)
+    assert M.sync_status() == M.MORPH_OK
+
+
+def test_wait_time_out_is_reported_and_device_stays_usable():
+    specs = [(300, 90, "erode", (3, 3), "rle", 0.3), (300, 90, "dilate", (3, 3), "packed", 0.3)]
+    jobs, imgs = make_jobs(specs)
+    # the second phase of the RLE job waits for one item more than exist
+    b = M.Batch(jobs, debug=[(0, 200_000_000), (1, 1)])
+    b.launch()
+    assert M.sync_status() == M.MORPH_ETIMEOUT
+    ok = M.Batch(jobs)
+    ok.launch()
+    assert M.sync_status() == M.MORPH_OK
+    check_all(jobs, imgs)
+
+
+def test_config4_like_sample():
+    """Twelve pages drawn like the uneven batch workload (sizes scaled down)."""
+    specs = []
+    for k, j in enumerate(synth.config4_jobs(12)):
+        W, H = j["W"] // 4, j["H"] // 4
+        specs.append((W, H, j["op"], j["se"], "rle" if k % 2 else "packed", j["density"]))
+    jobs, imgs = make_jobs(specs)
+    M.Batch(jobs).launch()
+    assert M.sync_status() == M.MORPH_OK
+    check_all(jobs, imgs)

@@ -155,6 +155,22 @@ MORPH_API morph_status morph_rect(int op, const morph_image *dst, const morph_im
 MORPH_API size_t morph_workspace_size(int op, const morph_image *dst, const morph_image *src,
                                       int se_w, int se_h, int origin_x, int origin_y);
 
+/* Erosion or dilation of an RLE image with no workspace and no allocation.
+ * The paper has no counterpart: this exists for callers that may not
+ * allocate device memory at all (a serving loop with a fixed budget, a host
+ * whose allocator owns the rest of the device).  Same result as
+ * morph_rect(MORPH_ERODE / MORPH_DILATE, ...) on RLE images; op must be one
+ * of those two.  The per-row scratch lives in a fixed array inside the
+ * library, so src->height must be <= 65536 (else MORPH_EINVAL); every device
+ * that loads the library holds that array (256 KiB) until exit.  The first
+ * call on a device looks up the array's device address (make that first
+ * call before any stream capture).  All calls on a device share the array:
+ * calls that overlap on the GPU race on it — serialise them.  Errors as for
+ * morph_rect; MORPH_ECAPACITY is latched on the device. */
+MORPH_API morph_status morph_rle_rect_noalloc(int op, const morph_image *dst,
+                                              const morph_image *src, int se_w, int se_h,
+                                              int origin_x, int origin_y, void *stream);
+
 /* ------------------------------------------------------------ conversion --
  * Section "Conversion Between Image Formats".
  * rle_from_bitmap: packed src -> RLE dst (canonical runs of every row).  A

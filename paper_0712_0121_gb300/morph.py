@@ -106,6 +106,8 @@ def _load():
     lib.morph_batch_plan_debug.restype = ci
     lib.morph_batch_launch.argtypes = [vp, vp, vp, sz, ci, vp]
     lib.morph_batch_launch.restype = ci
+    lib.morph_rle_rect_noalloc.argtypes = [ci, img_p, img_p, ci, ci, ci, ci, vp]
+    lib.morph_rle_rect_noalloc.restype = ci
     return lib
 
 
@@ -283,6 +285,19 @@ def morph_open_rect(dst, src, se_w, se_h, origin_x=None, origin_y=None, workspac
 
 def morph_close_rect(dst, src, se_w, se_h, origin_x=None, origin_y=None, workspace=None, stream=None):
     morph_rect(CLOSE, dst, src, se_w, se_h, origin_x, origin_y, workspace, stream)
+
+
+def rle_rect_noalloc(op, dst: "Rle", src: "Rle", se_w: int, se_h: int, origin_x=None,
+                     origin_y=None, stream=None) -> None:
+    """RLE erode or dilate without any workspace or allocation (for callers
+    that may not allocate device memory); images up to 65536 rows.  Calls that
+    overlap on the GPU share the library's fixed scratch and must not run
+    concurrently."""
+    ox = se_w // 2 if origin_x is None else origin_x
+    oy = se_h // 2 if origin_y is None else origin_y
+    _check(_lib.morph_rle_rect_noalloc(OPS.get(op, op), ctypes.byref(dst.desc()),
+                                       ctypes.byref(src.desc()), se_w, se_h, ox, oy,
+                                       _stream_handle(stream)))
 
 
 def convert_workspace_size(height: int) -> int:

@@ -136,9 +136,16 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- workload
+def pmap(fn, items):
+    """Map on host threads (the C page generator releases the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=min(32, cpu_count())) as ex:
+        return list(ex.map(fn, items))
+
+
 def make_pages(n, seed_base=0):
     from paper_0712_0121_gb300 import synth
-    return [synth.document_page(W, H, synth.seed_for(2, seed_base + k), 0.08)[0] for k in range(n)]
+    return pmap(lambda k: synth.document_page(W, H, synth.seed_for(2, seed_base + k), 0.08)[0], range(n))
 
 
 NW = (W + 63) // 64  # 64-bit words per row
@@ -179,6 +186,97 @@ def time_launches(fn, steps, stream):
         e.synchronize()
         times.append(s.elapsed_time(e))
     return times
+
+
+def run_uneven_batch(M, args, stream):
+    """Uneven batch: seeded pages of four sizes, ink density U(1,30) %, each
+    with its own rectangle and op; per-page path and band from the autotuner;
+    one persistent launch (CUDA graph) vs a loop of per-page launches."""
+    import torch
+    from paper_0712_0121_gb300 import autotune, synth
+    t0 = time.perf_counter()
+    specs = synth.config4_jobs(args.batch_pages)
+    tuner = autotune.Tuner(cache_path=args.tune_cache, pages_per_class=4, reps=2)
+    ref = (2550, 3300)
+    if not tuner.table:
+        tuner.tune_grid(ref[0], ref[1], synth.CONFIG4_OPS, synth.CONFIG4_SES,
+                        densities=(0.01, 0.05, 0.15, 0.3), bands=(64, 128, 256, 512))
+        tuner.save()
+    t_tune = time.perf_counter() - t0
+    imgs = pmap(lambda j: synth.config4_page(j)[0], specs)
+    jobs, npix, nrle = [], 0, 0
+    for j, img in zip(specs, imgs):
+        src = M.pack(img, 64)
+        dst = M.Packed.empty(j["W"], j["H"], 64)
+        path, band = tuner.choose(j["W"], j["H"], j["op"], j["se"], j["density"], ref_size=ref)
+        nrle += path == "rle"
+        jobs.append(dict(op=j["op"], se=j["se"], path=path, tile_rows=band, src=src, dst=dst))
+        npix += j["W"] * j["H"]
+    del imgs
+    batch = M.Batch(jobs)
+    graph = batch.capture()
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    tb = statistics.mean(time_launches(graph.replay, 5, stream))
+    ws = torch.empty(max(M.convert_workspace_size(6600), 1 << 20), dtype=torch.uint8, device="cuda")
+    rles = {}
+
+    def loop():
+        for j in jobs:
+            if j["path"] == "rle":
+                key = (j["src"].width, j["src"].height)
+                if key not in rles:
+                    cap = key[1] * (key[0] // 16 + 4)
+                    rles[key] = (M.Rle.empty(key[0], key[1], cap), M.Rle.empty(key[0], key[1], cap))
+                a, b = rles[key]
+                M.rle_from_bitmap(a, j["src"], ws)
+                M.morph_rect(j["op"], b, a, *j["se"])
+                M.rle_to_bitmap(j["dst"], b)
+            else:
+                M.morph_rect(j["op"], j["dst"], j["src"], *j["se"])
+
+    for _ in range(2):
+        loop()
+    torch.cuda.synchronize()
+    tl = statistics.mean(time_launches(loop, 3, stream))
+    st = M.sync_status()
+    return {"pages": len(jobs), "rle_path_pages": nrle, "megapixels": round(npix / 1e6, 1),
+            "batch_ms": round(tb, 3), "batch_pages_s": round(len(jobs) / tb * 1e3, 1),
+            "batch_gpix_s": round(npix / tb / 1e6, 1),
+            "per_page_loop_ms": round(tl, 3), "per_page_loop_pages_s": round(len(jobs) / tl * 1e3, 1),
+            "speedup": round(tl / tb, 2), "status": st, "tune_s": round(t_tune, 1)}
+
+
+def run_serving(M, args):
+    """Poisson arrivals of 5100x6600 pages (near-blank, text, halftone,
+    noise), pipeline close(31x1) -> open(3x3) -> dilate(1x15) -> RLE, 40 GB
+    budget: continuous batching vs an unbatched per-page server."""
+    import torch
+    from paper_0712_0121_gb300 import synth
+    from paper_0712_0121_gb300.serve import BatchExecutor, PerPageExecutor, Server, poisson_arrivals
+    PW, PH = 5100, 6600
+    pool = [M.pack(synth.config3_page(kind, page=0)[0], 64) for kind in synth.CONFIG3_KINDS]
+    bex = BatchExecutor(pool, PW, PH, n_slots=64, n_streams=4)
+    pex = PerPageExecutor(pool, PW, PH)
+    # warm-up both paths
+    Server(bex, 40e9).run(poisson_arrivals(2000.0, 16, 1), np.arange(16) % 4)
+    Server(pex, 40e9).run(poisson_arrivals(2000.0, 4, 1), np.arange(4) % 4)
+    torch.cuda.synchronize()
+    out = {}
+    for rate in (50, 200, 1000):
+        n = max(20, int(rate * args.serve_seconds))
+        arr = poisson_arrivals(float(rate), n, seed=5000 + rate)
+        pages = np.random.default_rng(rate).integers(0, len(pool), size=n)
+        sb = Server(bex, 40e9).run(arr, pages).summary()
+        sp = Server(pex, 40e9).run(arr, pages).summary()
+        keep = ("p50_ms", "p99_ms", "sustained_pages_s", "mean_batch", "max_in_flight")
+        out[str(rate)] = {"requests": n,
+                          "batched": {k: (round(sb[k], 3) if isinstance(sb[k], float) else sb[k]) for k in keep},
+                          "per_page": {k: (round(sp[k], 3) if isinstance(sp[k], float) else sp[k]) for k in keep}}
+    st = M.sync_status()
+    out["status"] = st
+    return out
 
 
 def run_ours(args):
@@ -325,6 +423,10 @@ def run_ours(args):
         "clocks": clocks,
         "generation_s": round(t_gen, 2),
     }
+    if not args.no_batch:
+        line["uneven_batch"] = run_uneven_batch(M, args, stream)
+    if not args.no_serve:
+        line["serving"] = run_serving(M, args)
     if rank == 0 and world == 1 and not args.no_cpu:
         cores = cpu_count()
         pix, dt, desc = oracle_sample(pages[:2], args.cpu_seconds, cores)
@@ -376,6 +478,11 @@ def main():
     ap.add_argument("--rle-runs-per-row", type=int, default=64)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the uneven-batch section")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
+    ap.add_argument("--batch-pages", type=int, default=256)
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--tune-cache", default=os.path.join("/tmp", "morph_tune_cache.json"))
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -79,7 +79,8 @@ typedef enum morph_op {
     MORPH_ERODE = 0,
     MORPH_DILATE = 1,
     MORPH_OPEN = 2,
-    MORPH_CLOSE = 3
+    MORPH_CLOSE = 3,
+    MORPH_TO_RLE = 4      /* batch jobs only: convert the packed src into the RLE dst */
 } morph_op;
 
 /* Descriptor of one image.  Only the fields of its format are read.
@@ -190,7 +191,10 @@ MORPH_API morph_status rle_to_bitmap(const morph_image *dst_packed, const morph_
 /* ----------------------------------------------------------------- batch --
  * Many uneven pages, each with its own op, rectangle and path, in ONE
  * persistent kernel launch.  A job reads a packed src page and writes a
- * packed dst page (same size, no overlap).  path MORPH_PATH_PACKED runs the
+ * packed dst page (same size, no overlap), or with MORPH_TO_RLE converts it
+ * into an RLE dst.  A job may depend on one earlier job (depends_on), which
+ * chains per-page pipelines (e.g. close -> open -> dilate -> to RLE) inside
+ * one launch; items are ordered so that every wait points backwards.  path MORPH_PATH_PACKED runs the
  * fused tile kernel on the page; MORPH_PATH_RLE converts the page to runs,
  * runs the RLE operation and converts back, all inside the same launch.  The
  * choice per page is the caller's (the Python autotuner picks it by ink
@@ -209,7 +213,8 @@ MORPH_API morph_status rle_to_bitmap(const morph_image *dst_packed, const morph_
  * than the plan's limit (4 s) latches MORPH_ETIMEOUT and stops every CTA; an RLE buffer that is
  * too small latches MORPH_ECAPACITY and leaves that job's dst unwritten.
  *
- * tile_rows: row-band height of packed tiles (0 = default).
+ * tile_rows: row-band height of packed tiles for jobs whose own tile_rows is
+ * 0 (0 = library default).
  * rle_runs_per_row: room per row in each RLE buffer of RLE-path jobs
  * (0 = W/16 + 4, at most ceil(W/2)).
  * Limits: packed-path rectangles must reach <= 128 pixels left and right of
@@ -218,11 +223,16 @@ MORPH_API morph_status rle_to_bitmap(const morph_image *dst_packed, const morph_
 typedef enum morph_path { MORPH_PATH_PACKED = 0, MORPH_PATH_RLE = 1 } morph_path;
 
 typedef struct morph_job {
-    int32_t op;          /* morph_op */
-    int32_t path;        /* morph_path */
-    int32_t se_w, se_h, origin_x, origin_y;
+    int32_t op;          /* morph_op; MORPH_TO_RLE converts src to an RLE dst */
+    int32_t path;        /* morph_path (ignored for MORPH_TO_RLE) */
+    int32_t se_w, se_h, origin_x, origin_y;   /* ignored for MORPH_TO_RLE */
+    int32_t depends_on;  /* index of an EARLIER job of the plan whose work must
+                            finish before this one starts (e.g. the job that
+                            writes this job's src), or -1 */
+    int32_t tile_rows;   /* packed path: row-band height of its tiles (0 = the
+                            plan's tile_rows, else the library default) */
     morph_image src;     /* packed */
-    morph_image dst;     /* packed, same size */
+    morph_image dst;     /* packed, same size; RLE for MORPH_TO_RLE */
 } morph_job;
 
 MORPH_API size_t morph_batch_plan_bytes(const morph_job *jobs, int n_jobs, int tile_rows,

@@ -6,8 +6,9 @@
 // An RLE job is a chain of phases — bitmap->RLE count, scan, write; per
 // erosion stage the run pass or between-line pass count, scan, write; RLE->
 // bitmap — whose items depend on every item of the job's previous phase.
-// Items are listed phase-major and claimed in list order from a device queue
-// by persistent CTAs.  An item waits (bounded spin with acquire loads) only
+// Items are listed by level (a job's phase index, shifted past the phases of
+// the job it depends on) and claimed in list order from a device queue by
+// persistent CTAs.  An item waits (bounded spin with acquire loads) only
 // for items of smaller index, which running CTAs have already claimed, so
 // the launch cannot deadlock; a wait that exceeds the time limit latches
 // MORPH_ETIMEOUT and makes every CTA stop.
@@ -40,10 +41,15 @@ enum ItemKind : int {
     IK_V_COUNT,
     IK_V_WRITE,
     IK_R2B,
+    IK_OUT_SCAN,   // MORPH_TO_RLE: scan into the caller's RLE dst
+    IK_OUT_WRITE,  // MORPH_TO_RLE: write the caller's runs
 };
 
 struct BatchJob {
     int32_t path;               // MORPH_PATH_PACKED / MORPH_PATH_RLE
+    int32_t dep;                // job that must finish first, or -1
+    int32_t level0;             // queue level of phase 0 (items sorted by level)
+    RleOut out;                 // MORPH_TO_RLE destination
     int32_t variant;            // packed tile variant
     int32_t nphase;
     int32_t phase_items[MAX_PH];
@@ -190,10 +196,16 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batch(const uint8_t *plan,
         const BatchJob &J = jobs[it.job];
         if (threadIdx.x == 0) {
             bool ok = true;
-            if (it.phase > 0)
+            if (it.phase > 0) {
                 ok = wait_count(done + (size_t)it.job * MAX_PH + it.phase - 1,
                                 J.phase_items[it.phase - 1], &ctrl->abort_flag, status,
                                 (unsigned long long)hdr->wait_limit_ns);
+            } else if (J.dep >= 0) {
+                const BatchJob &D = jobs[J.dep];
+                ok = wait_count(done + (size_t)J.dep * MAX_PH + D.nphase - 1,
+                                D.phase_items[D.nphase - 1], &ctrl->abort_flag, status,
+                                (unsigned long long)hdr->wait_limit_ns);
+            }
             s_ok = ok;
         }
         __syncthreads();
@@ -260,6 +272,19 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batch(const uint8_t *plan,
             va.out = reinterpret_cast<uint16_t *>(ws + (fromA ? J.off_runsB : J.off_runsA));
             va.write = it.kind == IK_V_WRITE;
             run_vpass(J.vkind[st], va, it.idx, sm);
+            break;
+        }
+        case IK_OUT_SCAN: {
+            scan_rows_block(reinterpret_cast<const int32_t *>(ws + J.off_counts), J.H, J.out.row_ptr,
+                            J.out.n_runs, J.out.capacity, status);
+            if (threadIdx.x == 0 && J.out.row_ptr[J.H] > J.out.capacity) atomicExch(overflow + it.job, 1);
+            break;
+        }
+        case IK_OUT_WRITE: {
+            if (ovf) break;
+            const int r0 = it.idx * RLE_ROWS_PER_ITEM;
+            b2r_write_rows(J.src, J.sstride, J.W, r0, min(J.H, r0 + RLE_ROWS_PER_ITEM),
+                           J.out.row_ptr, J.out.runs);
             break;
         }
         case IK_R2B: {
@@ -337,6 +362,33 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
         memset(&b, 0, sizeof(b));
         const morph_image &s = q.src, &d = q.dst;
         auto packed = [](const morph_image &m) { return m.fmt == MORPH_PACKED32 || m.fmt == MORPH_PACKED64; };
+        if (q.tile_rows < 0) return berr(MORPH_EINVAL, "tile_rows must be >= 0", j);
+        if (q.depends_on < -1 || q.depends_on >= j)
+            return berr(MORPH_EINVAL, "depends_on must be -1 or an earlier job", j);
+        b.dep = q.depends_on;
+        if (q.op == MORPH_TO_RLE) {
+            if (!packed(s) || d.fmt != MORPH_RLE) return berr(MORPH_EINVAL, "MORPH_TO_RLE needs a packed src and an RLE dst", j);
+            if (s.width < 1 || s.height < 1 || s.width != d.width || s.height != d.height || s.width > 65535)
+                return berr(MORPH_EINVAL, "bad or different sizes (RLE width <= 65535)", j);
+            const int Bs = s.fmt == MORPH_PACKED32 ? 32 : 64;
+            if (!s.words || s.stride_words < (s.width + Bs - 1) / Bs || (uintptr_t)s.words % (Bs / 8) ||
+                !d.row_ptr || d.capacity_runs < 0 || (d.capacity_runs > 0 && !d.runs) || s.reserved || d.reserved)
+                return berr(MORPH_EINVAL, "bad descriptor", j);
+            b.path = -1;
+            b.src = (const uint32_t *)s.words;
+            b.sstride = s.stride_words * (Bs / 32);
+            b.W = s.width;
+            b.H = s.height;
+            b.out = RleOut{d.row_ptr, d.runs, d.capacity_runs, d.n_runs};
+            b.off_counts = off;
+            off += al((size_t)b.H * 4);
+            const int rows_items = (b.H + RLE_ROWS_PER_ITEM - 1) / RLE_ROWS_PER_ITEM;
+            b.nphase = 3;
+            b.phase_kind[0] = IK_B2R_COUNT; b.phase_items[0] = rows_items; b.phase_stage[0] = -1;
+            b.phase_kind[1] = IK_OUT_SCAN;  b.phase_items[1] = 1;          b.phase_stage[1] = -1;
+            b.phase_kind[2] = IK_OUT_WRITE; b.phase_items[2] = rows_items; b.phase_stage[2] = -1;
+            continue;
+        }
         if (!packed(s) || !packed(d)) return berr(MORPH_EINVAL, "src and dst must be packed", j);
         if (s.width < 1 || s.height < 1 || s.width != d.width || s.height != d.height)
             return berr(MORPH_EINVAL, "bad or different sizes", j);
@@ -371,7 +423,8 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
             a.H = H;
             a.nw_valid = (W + 31) / 32;
             a.nw_cover = nw_cover;
-            if (packed_plan(a, q.op, c.sw, c.sh, c.ox, c.oy, tile_rows, MAX_THREADS) != 0)
+            if (packed_plan(a, q.op, c.sw, c.sh, c.ox, c.oy, q.tile_rows ? q.tile_rows : tile_rows,
+                            MAX_THREADS) != 0)
                 return berr(MORPH_EINVAL, "rectangle reaches more than 128 pixels sideways", j);
             b.variant = packed_variant(a);
             const dim3 g = packed_grid(a);
@@ -453,16 +506,24 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
         }
     }
     ws_total = off;
-    // phase-major item order: every item of phase p of a job comes after all
-    // items of its phase p-1
+    // Level order: phase p of job j sits at level level0_j + p, where a job
+    // that depends on job i starts one level after i's last phase.  Items are
+    // listed by level, so every item a wait refers to comes earlier in the
+    // list (and is already held by a running CTA when the wait starts).
     I.clear();
-    int maxph = 0;
-    for (auto &b : J) maxph = b.nphase > maxph ? b.nphase : maxph;
-    for (int p = 0; p < maxph; ++p)
-        for (int j = 0; j < n; ++j)
-            if (p < J[j].nphase)
+    int maxlevel = 0;
+    for (int j = 0; j < n; ++j) {
+        J[j].level0 = J[j].dep >= 0 ? J[J[j].dep].level0 + J[J[j].dep].nphase : 0;
+        const int top = J[j].level0 + J[j].nphase;
+        if (top > maxlevel) maxlevel = top;
+    }
+    for (int lv = 0; lv < maxlevel; ++lv)
+        for (int j = 0; j < n; ++j) {
+            const int p = lv - J[j].level0;
+            if (p >= 0 && p < J[j].nphase)
                 for (int k = 0; k < J[j].phase_items[p]; ++k)
                     I.push_back(BatchItem{j, (int16_t)p, (int16_t)J[j].phase_kind[p], k});
+        }
     return MORPH_OK;
 }
 

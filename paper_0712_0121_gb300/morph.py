@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(_PKG, "libmorph.so")
 
 MORPH_OK, MORPH_EINVAL, MORPH_ECAPACITY, MORPH_ENOMEM, MORPH_ECUDA, MORPH_ETIMEOUT = range(6)
 PACKED32, PACKED64, RLE = 0, 1, 2
-ERODE, DILATE, OPEN, CLOSE = 0, 1, 2, 3
+ERODE, DILATE, OPEN, CLOSE, TO_RLE = 0, 1, 2, 3, 4
 OPS = {"erode": ERODE, "dilate": DILATE, "open": OPEN, "close": CLOSE}
 PATH_PACKED, PATH_RLE = 0, 1
 
@@ -59,6 +59,8 @@ class morph_job(ctypes.Structure):
         ("se_h", ctypes.c_int32),
         ("origin_x", ctypes.c_int32),
         ("origin_y", ctypes.c_int32),
+        ("depends_on", ctypes.c_int32),
+        ("tile_rows", ctypes.c_int32),
         ("src", morph_image),
         ("dst", morph_image),
     ]
@@ -333,8 +335,11 @@ class Batch:
     """A persistent batch launch over many packed pages (``morph_batch_*``).
 
     ``jobs``: list of dicts with keys ``op`` ("erode"/"dilate"/"open"/"close"
-    or code), ``se`` ((se_w, se_h)), optional ``origin`` ((ox, oy), default
-    centre), ``path`` ("packed" or "rle"), ``src`` and ``dst`` (:class:`Packed`).
+    or code, or "to_rle"), ``se`` ((se_w, se_h); not for "to_rle"), optional
+    ``origin`` ((ox, oy), default centre), ``path`` ("packed" or "rle"),
+    ``src`` (:class:`Packed`), ``dst`` (:class:`Packed`, or :class:`Rle` for
+    "to_rle"), optional ``depends_on`` (index of an earlier job) and
+    ``tile_rows`` (row-band height of packed tiles).
     The plan is built on the host, copied to the device once, and every
     :meth:`launch` is one kernel launch (graph-capturable)."""
 
@@ -346,10 +351,12 @@ class Batch:
         arr = (morph_job * n)()
         self._keep = []
         for k, j in enumerate(jobs):
-            sw, sh = j["se"]
+            sw, sh = j.get("se", (1, 1))
             ox, oy = j.get("origin") or (sw // 2, sh // 2)
             path = j.get("path", "packed")
-            arr[k].op = OPS.get(j["op"], j["op"])
+            arr[k].op = TO_RLE if j["op"] == "to_rle" else OPS.get(j["op"], j["op"])
+            arr[k].depends_on = j.get("depends_on", -1)
+            arr[k].tile_rows = j.get("tile_rows", 0)
             arr[k].path = PATH_RLE if path in ("rle", PATH_RLE) else PATH_PACKED
             arr[k].se_w, arr[k].se_h, arr[k].origin_x, arr[k].origin_y = sw, sh, ox, oy
             arr[k].src = j["src"].desc()

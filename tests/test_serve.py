@@ -1,0 +1,80 @@
+"""Host logic of the serving loop (no GPU): admission under the memory
+budget, slot reuse, FIFO order, continuous batching of requests that arrive
+while others are in flight, and the latency statistics."""
+import numpy as np
+import pytest
+
+from paper_0712_0121_gb300.serve import Server, percentiles, poisson_arrivals
+
+
+class FakeClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        self.t += 1e-4          # every look at the clock advances 0.1 ms
+        return self.t
+
+
+class FakeExecutor:
+    """Each launch completes `service` seconds of fake time after it starts."""
+
+    def __init__(self, clock, slot_bytes=10, n_slots=8, service=2e-3):
+        self.clock, self.slot_bytes, self.n_slots, self.service = clock, slot_bytes, n_slots, service
+        self.launched = []
+
+    def launch(self, reqs):
+        self.launched.append([r.rid for r in reqs])
+        return (self.clock.t + self.service, reqs)
+
+    def done(self, h):
+        return self.clock.t >= h[0]
+
+    def release(self, h):
+        pass
+
+
+def run(rate=2000.0, n=200, budget=40, slot_bytes=10, n_slots=8, service=2e-3):
+    clk = FakeClock()
+    ex = FakeExecutor(clk, slot_bytes, n_slots, service)
+    srv = Server(ex, budget_bytes=budget, clock=clk, idle_sleep=0)
+    arr = poisson_arrivals(rate, n, seed=7)
+    st = srv.run(arr, np.zeros(n, int))
+    return srv, ex, st
+
+
+def test_every_request_completes_in_fifo_admission_order():
+    srv, ex, st = run()
+    assert st.completed == 200
+    order = [rid for b in ex.launched for rid in b]
+    assert order == sorted(order) == list(range(200))
+    assert all(r.done >= r.admitted >= r.arrival for r in srv.requests)
+
+
+def test_budget_is_never_exceeded_and_limits_slots():
+    srv, ex, st = run(budget=35, slot_bytes=10, n_slots=8)   # room for 3 requests
+    assert srv.n_slots == 3
+    assert st.max_in_flight <= 3
+    assert st.max_in_flight_bytes <= 35
+
+
+def test_requests_arriving_during_work_are_batched_together():
+    srv, ex, st = run(rate=20000.0, n=300, service=5e-3)
+    assert max(len(b) for b in ex.launched) > 1          # continuous batching happened
+    assert st.launches < 300
+    assert st.max_in_flight > 1                          # several launches overlapped
+
+
+def test_budget_smaller_than_a_request_is_rejected():
+    clk = FakeClock()
+    with pytest.raises(ValueError):
+        Server(FakeExecutor(clk, slot_bytes=100), budget_bytes=50, clock=clk)
+
+
+def test_percentiles_and_poisson_rate():
+    p = percentiles(list(range(1, 101)))
+    assert p["p50_ms"] == pytest.approx(50.5)
+    assert p["p99_ms"] == pytest.approx(99.01)
+    a = poisson_arrivals(1000.0, 20000, seed=3)
+    assert np.all(np.diff(a) > 0)
+    assert 20000 / a[-1] == pytest.approx(1000.0, rel=0.03)

@@ -18,6 +18,7 @@
 // launch can be captured in a CUDA graph and replayed.
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "packed_tile.cuh"
@@ -635,12 +636,24 @@ morph_status morph_batch_launch(const void *dev_plan, const void *host_plan, voi
     cudaError_t e = cudaSuccess;
     if (smem > 48 * 1024) e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess && n_ctas <= 0) {
+        // resident CTAs for this shared-memory size, cached per device
+        static std::mutex mu;
+        static int cached_smem[128], cached_ctas[128];
         int dev = 0, sms = 0, per_sm = 0;
         e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, BATCH_THREADS, smem);
-        n_ctas = sms * (per_sm > 0 ? per_sm : 1);
+        if (e == cudaSuccess && dev >= 0 && dev < 128) {
+            std::lock_guard<std::mutex> lk(mu);
+            if (cached_ctas[dev] > 0 && cached_smem[dev] == smem) {
+                n_ctas = cached_ctas[dev];
+            } else {
+                e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+                if (e == cudaSuccess)
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, BATCH_THREADS, smem);
+                n_ctas = sms * (per_sm > 0 ? per_sm : 1);
+                cached_smem[dev] = smem;
+                cached_ctas[dev] = n_ctas;
+            }
+        }
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(workspace, 0, (size_t)h->ws_ctrl_bytes, s);
     if (e == cudaSuccess) {

@@ -124,7 +124,7 @@ def _status_name(st: int) -> str:
     return _lib.morph_status_string(st).decode()
 
 
-def _check(st: int) -> None:
+def _check(st: int) -> None:  # noqa: D103
     if st != MORPH_OK:
         raise MorphError(st, _lib.morph_last_error().decode())
 

@@ -151,8 +151,11 @@ class Server:
                 break
             if time_limit is not None and now > time_limit:
                 break
-            if not batch and not pending:
-                time.sleep(self.idle_sleep) if self.idle_sleep else None
+            if not inflight and not pending and self.idle_sleep and nxt < len(reqs):
+                # idle: sleep until shortly before the next arrival, then spin
+                gap = reqs[nxt].arrival - (self.clock() - t0) - 2e-4
+                if gap > 0:
+                    time.sleep(min(gap, 1e-3))
         st.wall_s = (self.clock() - t0) - (reqs[0].arrival if reqs else 0.0)
         self.requests = reqs
         return st
@@ -176,56 +179,125 @@ class _Slots:
 class BatchExecutor:
     """Continuous batching: one persistent batch launch per admission round,
     on a pool of streams; each request's pipeline is chained jobs (the job
-    of step k depends on step k-1), ending with a bitmap->RLE job."""
+    of step k depends on step k-1), ending with a bitmap->RLE job.
+
+    Host cost per launch is kept small: the job descriptors of every
+    (slot, page) pair are built once; a round with one request reuses a plan
+    already on the device (launch = one memset + one kernel); a larger round
+    concatenates the cached descriptors, builds its plan in C into a pinned
+    staging buffer and uploads it asynchronously on the round's stream."""
 
     def __init__(self, pool, W, H, n_slots=64, pipeline=DEFAULT_PIPELINE, n_streams=4,
                  runs_per_row=None, path="packed", device="cuda"):
+        import ctypes
         import torch
         from . import morph as M
-        self.M, self.torch = M, torch
+        self.ct, self.M, self.torch = ctypes, M, torch
+        self.lib = M.lib()
         self.pool = pool                      # list of Packed pages on the device
         self.pipeline = pipeline
         self.path = path
         self.W, self.H = W, H
+        self.device = device
         rpr = runs_per_row if runs_per_row else W // 8 + 4
         self.slots = _Slots(M, torch, W, H, n_slots, len(pipeline), rpr, device)
         self.n_slots = n_slots
+        self.jpr = len(pipeline) + 1          # jobs per request
         self.streams = [torch.cuda.Stream(device=device) for _ in range(n_streams)]
         self.k = 0
-        ws_per_req = 4 * H + 1024
+        self._desc = {}                       # (slot, page) -> morph_job array of one request
+        self._plans = {}                      # (slot, page) -> (dev plan, host plan)
+        # sizes of the largest round (every slot in one launch)
+        big = self._array([(s, 0) for s in range(n_slots)])
+        self.max_plan = int(self.lib.morph_batch_plan_bytes(big, n_slots * self.jpr, 0, 0))
+        host = np.zeros(self.max_plan, np.uint8)
+        M._check(self.lib.morph_batch_plan_build(host.ctypes.data, self.max_plan, big,
+                                                 n_slots * self.jpr, 0, 0))
+        self.max_ws = int(self.lib.morph_batch_workspace_size(host.ctypes.data))
+        self.ws = [torch.empty(self.max_ws, dtype=torch.uint8, device=device) for _ in self.streams]
+        self.staging = [torch.empty(self.max_plan, dtype=torch.uint8, pin_memory=True)
+                        for _ in self.streams]
+        self.dplan = [torch.empty(self.max_plan, dtype=torch.uint8, device=device) for _ in self.streams]
+        self.staged = [None] * len(self.streams)
         self.slot_bytes = (len(pipeline) * self.slots.page_bytes + self.slots.cap * 4 + 4 * (H + 1)
-                           + ws_per_req)
+                           + self.max_ws // n_slots)
 
-    def jobs_for(self, r):
-        jobs = []
-        src = self.pool[r.page]
-        for k, (op, se) in enumerate(self.pipeline):
-            dst = self.slots.mid[r.slot][k]
-            jobs.append(dict(op=op, se=se, path=self.path, src=src, dst=dst,
-                             depends_on=(len(jobs) - 1) if k > 0 else -1))
-            src = dst
-        jobs.append(dict(op="to_rle", src=src, dst=self.slots.out[r.slot], depends_on=len(jobs) - 1))
-        return jobs
+    def _request_desc(self, slot, page):
+        key = (slot, page)
+        arr = self._desc.get(key)
+        if arr is None:
+            M = self.M
+            arr = (M.morph_job * self.jpr)()
+            src = self.pool[page]
+            for k, (op, (sw, sh)) in enumerate(self.pipeline):
+                j = arr[k]
+                j.op, j.path = M.OPS[op], (M.PATH_RLE if self.path == "rle" else M.PATH_PACKED)
+                j.se_w, j.se_h, j.origin_x, j.origin_y = sw, sh, sw // 2, sh // 2
+                j.depends_on = k - 1
+                j.src = src.desc()
+                dst = self.slots.mid[slot][k]
+                j.dst = dst.desc()
+                src = dst
+            j = arr[self.jpr - 1]
+            j.op, j.depends_on = M.TO_RLE, self.jpr - 2
+            j.se_w = j.se_h = 1
+            j.src = src.desc()
+            j.dst = self.slots.out[slot].desc()
+            self._desc[key] = arr
+        return arr
+
+    def _array(self, pairs):
+        ct = self.ct
+        n = len(pairs) * self.jpr
+        arr = (self.M.morph_job * n)()
+        size = ct.sizeof(self.M.morph_job) * self.jpr
+        for i, (slot, page) in enumerate(pairs):
+            ct.memmove(ct.addressof(arr) + i * size, self._request_desc(slot, page), size)
+            for k in range(self.jpr):
+                if arr[i * self.jpr + k].depends_on >= 0:
+                    arr[i * self.jpr + k].depends_on += i * self.jpr
+        return arr
 
     def launch(self, reqs):
-        jobs = []
-        for r in reqs:
-            base = len(jobs)
-            for j in self.jobs_for(r):
-                if j["depends_on"] >= 0:
-                    j["depends_on"] += base
-                jobs.append(j)
-        stream = self.streams[self.k % len(self.streams)]
+        torch, lib = self.torch, self.lib
+        si = self.k % len(self.streams)
         self.k += 1
-        with self.torch.cuda.stream(stream):
-            b = self.M.Batch(jobs)
-            b.launch(stream=stream)
-            ev = self.torch.cuda.Event()
-            ev.record(stream)
-        return (ev, b)
+        stream = self.streams[si]
+        h = stream.cuda_stream
+        if len(reqs) == 1:
+            key = (reqs[0].slot, reqs[0].page)
+            plan = self._plans.get(key)
+            if plan is None:
+                arr = self._request_desc(*key)
+                nb = int(lib.morph_batch_plan_bytes(arr, self.jpr, 0, 0))
+                host = np.zeros(nb, np.uint8)
+                self.M._check(lib.morph_batch_plan_build(host.ctypes.data, nb, arr, self.jpr, 0, 0))
+                plan = (torch.from_numpy(host).to(self.device), host)
+                self._plans[key] = plan
+            dev, host = plan
+            self.M._check(lib.morph_batch_launch(dev.data_ptr(), host.ctypes.data,
+                                                 self.ws[si].data_ptr(), self.max_ws, 0, h))
+        else:
+            arr = self._array([(r.slot, r.page) for r in reqs])
+            n = len(reqs) * self.jpr
+            if self.staged[si] is not None:
+                self.staged[si].synchronize()   # the previous upload from this buffer is done
+            stg = self.staging[si]
+            nb = int(lib.morph_batch_plan_bytes(arr, n, 0, 0))
+            self.M._check(lib.morph_batch_plan_build(stg.data_ptr(), nb, arr, n, 0, 0))
+            with torch.cuda.stream(stream):
+                self.dplan[si][:nb].copy_(stg[:nb], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(stream)
+            self.staged[si] = ev
+            self.M._check(lib.morph_batch_launch(self.dplan[si].data_ptr(), stg.data_ptr(),
+                                                 self.ws[si].data_ptr(), self.max_ws, 0, h))
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        return ev
 
     def done(self, h):
-        return h[0].query()
+        return h.query()
 
     def release(self, h):
         pass

@@ -87,14 +87,17 @@ Se clip_se(int W, int H, int sw, int sh, int ox, int oy) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct RleWs {
-    size_t counts, tmp_nruns, tmp_rowptr, tmp_runs, total;
+    size_t counts, bmp, tmp_nruns, tmp_rowptr, tmp_runs, total;
     int64_t tmp_capacity;
 };
 
+// counts int32[H] | output rows as bitmap words | (open/close) intermediate RLE
 RleWs rle_ws(int op, int W, int H) {
     RleWs w;
     w.counts = 0;
     size_t off = align256((size_t)H * sizeof(int32_t));
+    w.bmp = off;
+    off += align256((size_t)H * ((W + 31) / 32) * sizeof(uint32_t));
     w.tmp_capacity = 0;
     w.tmp_nruns = w.tmp_rowptr = w.tmp_runs = off;
     if (op == MORPH_OPEN || op == MORPH_CLOSE) {
@@ -257,21 +260,22 @@ morph_status run_rle(int op, const morph_image *dst, const morph_image *src, Se 
                     ws ? ws_bytes : (size_t)0, L.total);
     char *base = (char *)ws;
     int32_t *counts = (int32_t *)(base + L.counts);
+    uint32_t *bmp = (uint32_t *)(base + L.bmp);
     int *st = device_status_ptr();
     cudaError_t e;
     if (op == MORPH_ERODE || op == MORPH_DILATE) {
         e = launch_rle_rect(rle_in(src), rle_out(dst), op == MORPH_DILATE, se.sw, se.sh, se.ox,
-                            se.oy, counts, st, s);
+                            se.oy, counts, bmp, st, s);
     } else {
         RleOut tmp{(int32_t *)(base + L.tmp_rowptr), (uint16_t *)(base + L.tmp_runs),
                    L.tmp_capacity, (int64_t *)(base + L.tmp_nruns)};
         const int first_dilate = op == MORPH_CLOSE;
         e = launch_rle_rect(rle_in(src), tmp, first_dilate, se.sw, se.sh, se.ox, se.oy, counts,
-                            st, s);
+                            bmp, st, s);
         if (e == cudaSuccess) {
             RleIn tin{tmp.row_ptr, tmp.runs, W, H};
             e = launch_rle_rect(tin, rle_out(dst), !first_dilate, se.sw, se.sh, se.ox, se.oy,
-                                counts, st, s);
+                                counts, bmp, st, s);
         }
     }
     if (e != cudaSuccess) return cuda_fail(e, "RLE morphology launch");

@@ -4,8 +4,10 @@
 // The host builds a plan: a job table and a list of work items.  A packed
 // job is one phase of independent tiles (the fused tile of packed_tile.cuh).
 // An RLE job is a chain of phases — bitmap->RLE count, scan, write; per
-// erosion stage the run pass or between-line pass count, scan, write; RLE->
-// bitmap — whose items depend on every item of the job's previous phase.
+// erosion stage the run pass (count, scan, write) or the between-line pass
+// (rows to a bitmap with run counts, scan, encode; the last stage's rows go
+// straight to the job's packed output); RLE->bitmap after a run-pass stage —
+// whose items depend on every item of the job's previous phase.
 // Items are listed by level (a job's phase index, shifted past the phases of
 // the job it depends on) and claimed in list order from a device queue by
 // persistent CTAs.  An item waits (bounded spin with acquire loads) only
@@ -39,8 +41,8 @@ enum ItemKind : int {
     IK_B2R_WRITE,
     IK_ROW_COUNT,
     IK_ROW_WRITE,
-    IK_V_COUNT,
-    IK_V_WRITE,
+    IK_V_BMP,      // between-line pass: rows to a bitmap (+ run counts if not the last stage)
+    IK_BWRITE,     // encode the stored bitmap rows into runs
     IK_R2B,
     IK_OUT_SCAN,   // MORPH_TO_RLE: scan into the caller's RLE dst
     IK_OUT_WRITE,  // MORPH_TO_RLE: write the caller's runs
@@ -67,7 +69,7 @@ struct BatchJob {
     RowOp rop[2];
     VArgs va[2];                // pointers are filled on the device from ws offsets
     int32_t vkind[2];           // between-line variant (nwt, kmax)
-    int64_t off_counts, off_rpA, off_runsA, off_rpB, off_runsB, off_nA, off_nB;
+    int64_t off_counts, off_rpA, off_runsA, off_rpB, off_runsB, off_nA, off_nB, off_bmp;
     int64_t cap;                // runs capacity of each RLE buffer
 };
 
@@ -159,11 +161,13 @@ __device__ __noinline__ void vpass_fn(const VArgs &a, int bx, uint32_t *sm) {
 
 __device__ void run_vpass(int vkind, const VArgs &a, int bx, uint32_t *sm) {
     switch (vkind) {
-    case 0: vpass_fn<2, 3>(a, bx, sm); break;
-    case 1: vpass_fn<2, 6>(a, bx, sm); break;
-    case 2: vpass_fn<2, 16>(a, bx, sm); break;
-    case 3: vpass_fn<8, 3>(a, bx, sm); break;
-    case 4: vpass_fn<8, 6>(a, bx, sm); break;
+    case 0: vpass_fn<2, 2>(a, bx, sm); break;
+    case 1: vpass_fn<2, 3>(a, bx, sm); break;
+    case 2: vpass_fn<2, 6>(a, bx, sm); break;
+    case 3: vpass_fn<2, 16>(a, bx, sm); break;
+    case 4: vpass_fn<8, 2>(a, bx, sm); break;
+    case 5: vpass_fn<8, 3>(a, bx, sm); break;
+    case 6: vpass_fn<8, 6>(a, bx, sm); break;
     default: vpass_fn<8, 16>(a, bx, sm); break;
     }
 }
@@ -260,19 +264,35 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batch(const uint8_t *plan,
                          min(J.H, r0 + RLE_ROWS_PER_ITEM));
             break;
         }
-        case IK_V_COUNT:
-        case IK_V_WRITE: {
+        case IK_V_BMP: {
             if (ovf) break;
             const int st = J.phase_stage[it.phase];
             const bool fromA = st == 0;
             VArgs va = J.va[st];
             va.in.row_ptr = reinterpret_cast<const int32_t *>(ws + (fromA ? J.off_rpA : J.off_rpB));
             va.in.runs = reinterpret_cast<const uint16_t *>(ws + (fromA ? J.off_runsA : J.off_runsB));
-            va.counts = reinterpret_cast<int32_t *>(ws + J.off_counts);
-            va.out_row_ptr = reinterpret_cast<const int32_t *>(ws + (fromA ? J.off_rpB : J.off_rpA));
-            va.out = reinterpret_cast<uint16_t *>(ws + (fromA ? J.off_runsB : J.off_runsA));
-            va.write = it.kind == IK_V_WRITE;
+            if (st == J.nst - 1) {
+                // last stage: the rows go straight to the job's packed output
+                va.bmp = J.dst;
+                va.bmp_stride = J.dstride;
+                va.bmp_words = J.nw_cover;
+                va.counts = nullptr;
+            } else {
+                va.bmp = reinterpret_cast<uint32_t *>(ws + J.off_bmp);
+                va.bmp_stride = (J.W + 31) / 32;
+                va.bmp_words = (J.W + 31) / 32;
+                va.counts = reinterpret_cast<int32_t *>(ws + J.off_counts);
+            }
             run_vpass(J.vkind[st], va, it.idx, sm);
+            break;
+        }
+        case IK_BWRITE: {
+            if (ovf) break;
+            const int r0 = it.idx * RLE_ROWS_PER_ITEM;
+            b2r_write_rows(reinterpret_cast<const uint32_t *>(ws + J.off_bmp), (J.W + 31) / 32, J.W, r0,
+                           min(J.H, r0 + RLE_ROWS_PER_ITEM),
+                           reinterpret_cast<const int32_t *>(ws + J.off_rpB),
+                           reinterpret_cast<uint16_t *>(ws + J.off_runsB));
             break;
         }
         case IK_OUT_SCAN: {
@@ -456,6 +476,10 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
             b.off_rpB = off; off += al((size_t)(H + 1) * 4);
             b.off_runsA = off; off += al((size_t)b.cap * 4);
             b.off_runsB = off; off += al((size_t)b.cap * 4);
+            if (b.nst == 2 && c.sh > 1) {
+                b.off_bmp = off;
+                off += al((size_t)H * ((W + 31) / 32) * 4);
+            }
             const int rows_items = (H + RLE_ROWS_PER_ITEM - 1) / RLE_ROWS_PER_ITEM;
             int p = 0;
             auto add = [&](int kind, int items, int stage) {
@@ -490,15 +514,20 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
                     vpass_plan(v, W, H, c.sh);
                     v.capacity = b.cap;
                     const int km = vpass_kmax(v.K);
-                    b.vkind[st] = (v.nwt == 2 ? 0 : 3) + (km == 3 ? 0 : (km == 6 ? 1 : 2));
+                    b.vkind[st] = (v.nwt == 2 ? 0 : 4) + (km == 2 ? 0 : (km == 3 ? 1 : (km == 6 ? 2 : 3)));
                     const int sb = (int)vpass_smem_bytes(v);
                     if (sb > smem) smem = sb;
-                    add(IK_V_COUNT, vpass_grid(v), st);
-                    add(IK_SCAN, 1, st);
-                    add(IK_V_WRITE, vpass_grid(v), st);
+                    // rows -> bitmap; an intermediate stage is then encoded
+                    // into runs (its run pass input for the next stage), the
+                    // last stage's bitmap is the job's output
+                    add(IK_V_BMP, vpass_grid(v), st);
+                    if (st < b.nst - 1) {
+                        add(IK_SCAN, 1, st);
+                        add(IK_BWRITE, rows_items, st);
+                    }
                 }
             }
-            add(IK_R2B, rows_items, -1);
+            if (c.sh == 1) add(IK_R2B, rows_items, -1);
             b.nphase = p;
             const int sb = 8 * nw_cover * 4;
             if (sb > smem) smem = sb;

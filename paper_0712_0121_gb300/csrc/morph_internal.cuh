@@ -115,6 +115,15 @@ struct VArgs {
     int nw_ext;              // words covering positions 0..W
     int nwt;                 // words per thread (2 or 8)
     int tpr, groups, band, rb, slot_words;
+    // Output, one of two modes:
+    //  bitmap mode (bmp != nullptr): every output row is stored as packed
+    //    words (bmp_words per row, stride bmp_stride, padding zero) and, when
+    //    counts != nullptr, its run count goes to counts[y];
+    //  run mode (bmp == nullptr): write == 0 counts runs into counts[y];
+    //    write == 1 encodes the runs at out_row_ptr[y] into out.
+    uint32_t *bmp;
+    int64_t bmp_stride;
+    int bmp_words;
     int write;
     int32_t *counts;
     const int32_t *out_row_ptr;
@@ -138,7 +147,10 @@ cudaError_t launch_rle_to_bitmap(RleIn in, uint32_t *dst, int64_t dstride, int n
                                  cudaStream_t s);
 // One erode (dilate=0) or dilate (dilate=1) of an RLE image by a sw x sh
 // rectangle with origin (ox, oy).  counts: int32[H] scratch.
+// bmp_scratch: W*H/8 bytes (rows of ceil(W/32) u32 words) for the bitmap
+// mode of the between-line pass; nullptr runs it in run mode (count pass,
+// then a write pass that recomputes the rows and encodes them).
 cudaError_t launch_rle_rect(RleIn in, RleOut out, int dilate, int sw, int sh, int ox, int oy,
-                            int32_t *counts, int *status, cudaStream_t s);
+                            int32_t *counts, uint32_t *bmp_scratch, int *status, cudaStream_t s);
 
 }  // namespace morph

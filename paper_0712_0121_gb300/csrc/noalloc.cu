@@ -120,7 +120,7 @@ extern "C" morph_status morph_rle_rect_noalloc(int op, const morph_image *dst,
 
     const RleIn in{src->row_ptr, src->runs, W, H};
     const RleOut out{dst->row_ptr, dst->runs, dst->capacity_runs, dst->n_runs};
-    e = launch_rle_rect(in, out, op == MORPH_DILATE, l + r + 1, u + d + 1, l, u, counts,
+    e = launch_rle_rect(in, out, op == MORPH_DILATE, l + r + 1, u + d + 1, l, u, counts, nullptr,
                         device_status_ptr(), (cudaStream_t)stream);
     if (e != cudaSuccess) return reject(MORPH_ECUDA, "RLE morphology launch: %s", cudaGetErrorString(e));
     return MORPH_OK;

@@ -34,6 +34,7 @@
 // rows; a band first sweeps nst*(sh-1) warm-up rows.
 #pragma once
 
+#include "counters.cuh"
 #include "morph_internal.cuh"
 
 namespace morph {
@@ -150,42 +151,6 @@ __device__ __forceinline__ void h_left(const uint32_t (&W)[NWT + 2 * HALO], uint
         out[t] = B[HALO + t] & sh;
     }
 }
-
-// Bit-sliced counter of consecutive 1-rows; push returns "count >= sh".
-// KMAX == 2 (sh = 2 or 3) keeps the last rows instead: the AND of the window
-// directly (c[0] = previous row, c[1] = the row before).
-template <int KMAX>
-struct ColCounter {
-    uint32_t c[KMAX];
-    uint32_t sat;
-    __device__ __forceinline__ void reset() {
-#pragma unroll
-        for (int k = 0; k < KMAX; ++k) c[k] = 0;
-        sat = 0;
-    }
-    __device__ __forceinline__ uint32_t push(uint32_t v, int K, const uint32_t (&eqm)[KMAX]) {
-        if (KMAX == 2) {
-            // eqm[0] == 0 means bit 0 of sh is set: sh == 3 (K == 2) or sh == 1
-            const uint32_t e = v & c[0] & (eqm[0] ? ONES : c[KMAX - 1]);
-            c[KMAX - 1] = c[0];
-            c[0] = v;
-            return e;
-        }
-        uint32_t carry = v, eq = ONES;
-#pragma unroll
-        for (int k = 0; k < KMAX; ++k) {
-            if (k < K || KMAX <= 6) {  // planes above K stay zero and never match
-                const uint32_t ck = c[k];
-                const uint32_t nk = (ck ^ carry) & v;
-                carry = ck & carry;
-                c[k] = nk;
-                eq &= nk ^ eqm[k];
-            }
-        }
-        sat = v & (sat | eq);
-        return sat;
-    }
-};
 
 struct HPlan {  // one horizontal erosion stage
     int L, R, mL, mR, fL, fR;

@@ -75,6 +75,7 @@ cudaError_t launch_vt(const VArgs &a, cudaStream_t s) {
 template <int NWT>
 cudaError_t launch_vk(const VArgs &a, cudaStream_t s) {
     switch (vpass_kmax(a.K)) {
+    case 2: return launch_vt<NWT, 2>(a, s);
     case 3: return launch_vt<NWT, 3>(a, s);
     case 6: return launch_vt<NWT, 6>(a, s);
     default: return launch_vt<NWT, 16>(a, s);
@@ -83,7 +84,7 @@ cudaError_t launch_vk(const VArgs &a, cudaStream_t s) {
 
 }  // namespace
 
-int vpass_kmax(int K) { return K <= 3 ? 3 : (K <= 6 ? 6 : 16); }
+int vpass_kmax(int K) { return K <= 2 ? 2 : (K <= 3 ? 3 : (K <= 6 ? 6 : 16)); }
 
 void vpass_plan(VArgs &a, int W, int H, int sh) {
     a.nw_ext = (W >> 5) + 1;
@@ -92,8 +93,8 @@ void vpass_plan(VArgs &a, int W, int H, int sh) {
     a.groups = MAX_THREADS / a.tpr;
     if (a.groups < 1) a.groups = 1;
     a.rb = a.nwt == 2 ? 8 : 4;
-    int band = 4 * (sh - 1);
-    if (band < 32) band = 32;
+    int band = 8 * (sh - 1);
+    if (band < 64) band = 64;
     if (band > 1024) band = 1024;
     a.band = band;
     if (a.groups * a.band > H) {
@@ -104,7 +105,8 @@ void vpass_plan(VArgs &a, int W, int H, int sh) {
 }
 
 size_t vpass_smem_bytes(const VArgs &a) {
-    return (size_t)2 * a.rb * a.groups * a.slot_words * sizeof(uint32_t);
+    const size_t nslot = (size_t)a.rb * a.groups;
+    return 2 * nslot * a.slot_words * sizeof(uint32_t) + (2 * nslot + 2) * sizeof(int);
 }
 int vpass_threads(const VArgs &a) { return ((a.groups * a.tpr + 31) / 32) * 32; }
 int vpass_grid(const VArgs &a) { return (a.in.H + a.groups * a.band - 1) / (a.groups * a.band); }
@@ -130,7 +132,7 @@ cudaError_t launch_rle_to_bitmap(RleIn in, uint32_t *dst, int64_t dstride, int n
 }
 
 cudaError_t launch_rle_rect(RleIn in, RleOut out, int dilate, int sw, int sh, int ox, int oy,
-                            int32_t *counts, int *status, cudaStream_t s) {
+                            int32_t *counts, uint32_t *bmp_scratch, int *status, cudaStream_t s) {
     RowOp op;
     op.dilate = dilate;
     op.sw = sw;
@@ -153,7 +155,24 @@ cudaError_t launch_rle_rect(RleIn in, RleOut out, int dilate, int sw, int sh, in
     for (int k = 0; k < 16; ++k) a.eqm[k] = ((sh >> k) & 1) ? 0u : ONES;
     vpass_plan(a, in.W, in.H, sh);
     a.counts = counts;
+    a.bmp = nullptr;
+    a.bmp_stride = 0;
+    a.bmp_words = 0;
     a.write = 0;
+    if (bmp_scratch) {
+        // one between-line pass: rows as bitmap words plus run counts; then
+        // the prefix sum and a transition encode of the stored rows
+        const int nwv = (in.W + 31) / 32;
+        a.bmp = bmp_scratch;
+        a.bmp_stride = nwv;
+        a.bmp_words = nwv;
+        cudaError_t e = a.nwt == 2 ? launch_vk<2>(a, s) : launch_vk<8>(a, s);
+        if (e != cudaSuccess) return e;
+        k_scan_rows<<<1, 1024, 0, s>>>(counts, in.H, out.row_ptr, out.n_runs, out.capacity, status);
+        k_b2r_write<<<row_items(in.H), 256, 0, s>>>(bmp_scratch, nwv, in.W, in.H, out.row_ptr,
+                                                     out.capacity, out.runs);
+        return cudaGetLastError();
+    }
     a.out_row_ptr = out.row_ptr;
     a.capacity = out.capacity;
     a.out = out.runs;

@@ -11,6 +11,7 @@
 // count -> exclusive prefix sum over rows -> write.
 #pragma once
 
+#include "counters.cuh"
 #include "morph_internal.cuh"
 
 namespace morph {
@@ -251,9 +252,10 @@ __device__ __forceinline__ void rowpass_rows(const RleIn &in, const RowOp &op, i
 //   turns transitions into pixels (prefix XOR); P4 every thread pushes its
 //   words into bit-sliced counters of consecutive covered rows — the "count
 //   reached sh" plane is the output row, i.e. the intersection of the sh
-//   neighbouring rows' intervals; P5 one warp per output row finds its
-//   transitions and counts them (count pass) or writes them at row_ptr
-//   (write pass).  sm: 2 * rb * groups * slot_words words.
+//   neighbouring rows' intervals; P5 one warp per output row either stores
+//   the row as packed words (bitmap mode, with its run count if asked) or
+//   finds its transitions and counts them (count pass) or writes them at
+//   row_ptr (write pass).  sm: 2 * rb * groups * slot_words words.
 template <int NWT, int KMAX>
 __device__ __forceinline__ void vpass_tile(const VArgs &a, int bx, uint32_t *sm) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -268,31 +270,64 @@ __device__ __forceinline__ void vpass_tile(const VArgs &a, int bx, uint32_t *sm)
     const int Ybase = bx * a.groups * a.band;
     const int iters = a.band + a.sh - 1;
 
-    uint32_t vmask[NWT], c[NWT][KMAX], sat[NWT];
+    uint32_t vmask[NWT], eqm[KMAX];
+    ColCounter<KMAX> cc[NWT];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) eqm[k] = a.eqm[k];
 #pragma unroll
     for (int t = 0; t < NWT; ++t) {
         const int w = lt * NWT + t;
         vmask[t] = (act && w < nw_valid) ? word_mask(w, W) : 0u;
-        sat[t] = 0;
-#pragma unroll
-        for (int k = 0; k < KMAX; ++k) c[t][k] = 0;
+        cc[t].reset();
     }
+    const uint32_t invm = a.inv ? ONES : 0u;
+    // run ranges of the chunk's input rows: start and exclusive prefix of counts
+    int *sA = reinterpret_cast<int *>(O + (size_t)nslot * slot);
+    int *sP = sA + nslot + 1;
 
     for (int c0 = 0; c0 < iters; c0 += a.rb) {
-        // P1: clear transition slots
+        // P1: clear transition slots; read the run range of every slot's row
         for (int q = tid; q < nslot * slot; q += blockDim.x) T[q] = 0;
-        __syncthreads();
-        // P2: kept transitions of every input row of the chunk
-        for (int q = 0; q < nslot; ++q) {
+        for (int q = tid; q < nslot; q += blockDim.x) {
             const int i = q / a.groups, gq = q - i * a.groups;
-            if (gq != g || !act) continue;
             const int r = Ybase + gq * a.band - a.ey + c0 + i;
-            if (r < 0 || r >= H) continue;
-            const int64_t ra = a.in.row_ptr[r], rb_ = a.in.row_ptr[r + 1];
-            uint32_t *slotp = T + (size_t)q * slot;
+            int r0 = 0, n = 0;
+            if (r >= 0 && r < H) {
+                r0 = a.in.row_ptr[r];
+                n = a.in.row_ptr[r + 1] - r0;
+            }
+            sA[q] = r0;
+            sP[q] = n;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            int carry = 0;
+            for (int q0 = 0; q0 < nslot; q0 += 32) {
+                const int q = q0 + lane;
+                const int n = q < nslot ? sP[q] : 0;
+                int tot;
+                const int ex = warp_excl_scan(n, lane, tot);
+                if (q < nslot) sP[q] = carry + ex;
+                carry += tot;
+            }
+            if (lane == 0) sP[nslot] = carry;
+        }
+        __syncthreads();
+        // P2: every run of the chunk is an independent item: its kept
+        // transitions (after the within-line pass) are XORed into its slot
+        {
+            const int total = sP[nslot];
             const int nbits = 32 * slot;
-            for (int64_t j = ra + lt; j < rb_; j += a.tpr) {
-                const RunT rt = row_op(a.in.runs, j, ra, rb_, a.op);
+            for (int gi = tid; gi < total; gi += blockDim.x) {
+                int lo = 0, hi = nslot;  // sP[lo] <= gi < sP[hi]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (sP[mid] <= gi) lo = mid;
+                    else hi = mid;
+                }
+                const int64_t ra = sA[lo], rb_ = ra + (sP[lo + 1] - sP[lo]);
+                const RunT rt = row_op(a.in.runs, ra + (gi - sP[lo]), ra, rb_, a.op);
+                uint32_t *slotp = T + (size_t)lo * slot;
                 // the bounds guards only matter for a non-canonical input list
                 if (rt.ks && rt.s >= 0 && rt.s < nbits) atomicXor(slotp + (rt.s >> 5), 1u << (rt.s & 31));
                 if (rt.ke && rt.e >= 0 && rt.e < nbits) atomicXor(slotp + (rt.e >> 5), 1u << (rt.e & 31));
@@ -322,24 +357,8 @@ __device__ __forceinline__ void vpass_tile(const VArgs &a, int bx, uint32_t *sm)
                 uint32_t *op = O + (size_t)(i * a.groups + g) * slot + lt * NWT;
 #pragma unroll
                 for (int t = 0; t < NWT; ++t) {
-                    uint32_t v = ONES;
-                    if (rin) {
-                        const uint32_t x = tp[t];
-                        v = (a.inv ? ~x : x) | ~vmask[t];
-                    }
-                    uint32_t carry = v, eq = ONES;
-#pragma unroll
-                    for (int k = 0; k < KMAX; ++k) {
-                        if (k < a.K) {
-                            const uint32_t ck = c[t][k];
-                            const uint32_t nk = (ck ^ carry) & v;
-                            carry = ck & carry;
-                            c[t][k] = nk;
-                            eq &= nk ^ a.eqm[k];
-                        }
-                    }
-                    sat[t] = v & (sat[t] | eq);
-                    op[t] = (a.inv ? ~sat[t] : sat[t]) & vmask[t];
+                    const uint32_t v = rin ? ((tp[t] ^ invm) | ~vmask[t]) : ONES;
+                    op[t] = (cc[t].push(v, a.K, eqm) ^ invm) & vmask[t];
                 }
             }
         }
@@ -352,6 +371,27 @@ __device__ __forceinline__ void vpass_tile(const VArgs &a, int bx, uint32_t *sm)
             const int y = y0 + it - (a.sh - 1);
             if (it < a.sh - 1 || y >= y0 + a.band || y >= H) continue;
             const uint32_t *op = O + (size_t)q * slot;
+            if (a.bmp) {
+                // bitmap mode: store the row's words, count its runs if asked
+                uint32_t *row = a.bmp + (int64_t)y * a.bmp_stride;
+                const int kmax = a.nw_ext > a.bmp_words ? a.nw_ext : a.bmp_words;
+                int cnt = 0;
+                for (int k0 = 0; k0 < kmax; k0 += 32) {
+                    const int k = k0 + lane;
+                    const uint32_t w = k < a.nw_ext ? op[k] : 0u;
+                    if (k < a.bmp_words) row[k] = k < nw_valid ? w : 0u;
+                    if (a.counts && k < a.nw_ext) {
+                        const uint32_t p = k > 0 ? op[k - 1] : 0u;
+                        cnt += __popc(w ^ ((w << 1) | (p >> 31)));
+                    }
+                }
+                if (a.counts) {
+#pragma unroll
+                    for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(FULL_MASK, cnt, o);
+                    if (lane == 0) a.counts[y] = cnt >> 1;
+                }
+                continue;
+            }
             int64_t pos0 = a.write ? 2 * (int64_t)a.out_row_ptr[y] : 0;
             int cnt = 0;
             for (int k0 = 0; k0 < a.nw_ext; k0 += 32) {

@@ -279,6 +279,59 @@ def run_serving(M, args):
     return out
 
 
+def run_probe(args):
+    """Standalone operations, repeated, on a tall stack of distinct letter
+    pages (more than L2): a target for ncu captures of a single kernel, and
+    a timing of each kernel alone (CUDA events, median of the repetitions)
+    with its algorithmic bytes against the measured HBM copy bandwidth."""
+    import torch
+    from paper_0712_0121_gb300 import morph as M
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    pages = make_pages(16)
+    img = np.concatenate([pages[k % 16] for k in range(args.probe_pages)], axis=0)
+    Ht, Wt = img.shape
+    src = M.pack(img, 64)
+    page_bytes = src.words.numel() * 8
+    peak = 6782.1
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        pass
+    results = []
+    for se in args.probe_se.split(","):
+        sw, sh = (int(v) for v in se.split("x"))
+        if args.probe == "packed":
+            dst = M.Packed.empty(Wt, Ht, 64)
+            fn = lambda: M.morph_rect(args.probe_op, dst, src, sw, sh)  # noqa: E731
+            alg = 2 * page_bytes
+        else:
+            cap = Ht * args.rle_runs_per_row
+            a, b = M.Rle.empty(Wt, Ht, cap), M.Rle.empty(Wt, Ht, cap)
+            out = M.Packed.empty(Wt, Ht, 64)
+            ws = torch.empty(M.workspace_size(args.probe_op, b, a, sw, sh), dtype=torch.uint8, device="cuda")
+            cws = torch.empty(M.convert_workspace_size(Ht), dtype=torch.uint8, device="cuda")
+
+            def fn():
+                M.rle_from_bitmap(a, src, cws)
+                M.morph_rect(args.probe_op, b, a, sw, sh, workspace=ws)
+                M.rle_to_bitmap(out, b)
+            alg = 2 * page_bytes
+        fn()
+        torch.cuda.synchronize()
+        ms = statistics.median(time_launches(fn, args.probe_reps, stream))
+        st = M.sync_status()
+        results.append({"se": se, "ms": round(ms, 4), "gpix_s": round(Wt * Ht / ms / 1e6, 1),
+                        "alg_gb_s": round(alg / ms / 1e6, 1), "frac": round(alg / ms / 1e6 / peak, 3),
+                        "status": st})
+        if st != M.MORPH_OK:
+            print(json.dumps(results[-1]))
+            raise SystemExit(1)
+    print(json.dumps({"probe": args.probe, "op": args.probe_op, "width": Wt, "height": Ht,
+                      "peak_gb_s": peak, "results": results}))
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -483,10 +536,18 @@ def main():
     ap.add_argument("--batch-pages", type=int, default=256)
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--tune-cache", default=os.path.join("/tmp", "morph_tune_cache.json"))
+    ap.add_argument("--probe", choices=["packed", "rle"], default=None,
+                    help="run one standalone op on a tall page stack (ncu target) and exit")
+    ap.add_argument("--probe-op", default="erode")
+    ap.add_argument("--probe-se", default="3x3")
+    ap.add_argument("--probe-pages", type=int, default=160)
+    ap.add_argument("--probe-reps", type=int, default=4)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.impl == "reference":
+    if args.probe:
+        run_probe(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

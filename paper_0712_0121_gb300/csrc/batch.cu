@@ -338,7 +338,7 @@ int packed_variant(const PackedArgs &a) {
     const int kidx = [&] {
         const int km = packed_kmax(a);
         if (km == 0) return 0;
-        if (km == 2) return 1;
+        if (km == 2) return 1;  // sh == 3 window
         if (km <= 6) return 2;
         return 3;
     }();
@@ -513,7 +513,7 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
                     for (int k = 0; k < 16; ++k) v.eqm[k] = ((c.sh >> k) & 1) ? 0u : ONES;
                     vpass_plan(v, W, H, c.sh);
                     v.capacity = b.cap;
-                    const int km = vpass_kmax(v.K);
+                    const int km = vpass_kmax(c.sh);
                     b.vkind[st] = (v.nwt == 2 ? 0 : 4) + (km == 2 ? 0 : (km == 3 ? 1 : (km == 6 ? 2 : 3)));
                     const int sb = (int)vpass_smem_bytes(v);
                     if (sb > smem) smem = sb;

@@ -7,8 +7,8 @@
 namespace morph {
 
 // Bit-sliced counter of consecutive 1-rows; push returns "count >= sh".
-// KMAX == 2 (sh = 2 or 3) keeps the last rows instead: the AND of the window
-// directly (c[0] = previous row, c[1] = the row before).
+// KMAX == 2 is only used for sh == 3 and keeps the last two rows instead:
+// the AND of the window directly (c[0] = previous row, c[1] = the one before).
 template <int KMAX>
 struct ColCounter {
     uint32_t c[KMAX];
@@ -20,9 +20,8 @@ struct ColCounter {
     }
     __device__ __forceinline__ uint32_t push(uint32_t v, int K, const uint32_t (&eqm)[KMAX]) {
         if (KMAX == 2) {
-            // eqm[0] == 0 means bit 0 of sh is set: sh == 3 (K == 2) or sh == 1
-            const uint32_t e = v & c[0] & (eqm[0] ? ONES : c[KMAX - 1]);
-            c[KMAX - 1] = c[0];
+            const uint32_t e = v & c[0] & c[1];
+            c[1] = c[0];
             c[0] = v;
             return e;
         }

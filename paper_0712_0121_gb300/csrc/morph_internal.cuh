@@ -137,7 +137,7 @@ void vpass_plan(VArgs &a, int W, int H, int sh);
 size_t vpass_smem_bytes(const VArgs &a);
 int vpass_threads(const VArgs &a);
 int vpass_grid(const VArgs &a);
-int vpass_kmax(int K);
+int vpass_kmax(int sh);  // counter width for a window of sh rows
 // rows handled by one work item of the row-wise RLE kernels
 constexpr int RLE_ROWS_PER_ITEM = 64;
 

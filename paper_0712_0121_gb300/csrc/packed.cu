@@ -70,7 +70,8 @@ int packed_halo(int sw, int ex) {
 
 int packed_kmax(const PackedArgs &a) {
     if (a.sh == 1) return 0;
-    if (a.K <= 2) return 2;
+    if (a.sh == 3) return 2;  // two-row register window
+    if (a.K <= 2) return 3;
     if (a.K <= 3) return 3;
     if (a.K <= 4) return 4;
     if (a.K <= 6) return 6;

@@ -74,7 +74,7 @@ cudaError_t launch_vt(const VArgs &a, cudaStream_t s) {
 
 template <int NWT>
 cudaError_t launch_vk(const VArgs &a, cudaStream_t s) {
-    switch (vpass_kmax(a.K)) {
+    switch (vpass_kmax(a.sh)) {
     case 2: return launch_vt<NWT, 2>(a, s);
     case 3: return launch_vt<NWT, 3>(a, s);
     case 6: return launch_vt<NWT, 6>(a, s);
@@ -84,7 +84,10 @@ cudaError_t launch_vk(const VArgs &a, cudaStream_t s) {
 
 }  // namespace
 
-int vpass_kmax(int K) { return K <= 2 ? 2 : (K <= 3 ? 3 : (K <= 6 ? 6 : 16)); }
+int vpass_kmax(int sh) {
+    const int K = bit_length(sh);
+    return sh == 3 ? 2 : (K <= 3 ? 3 : (K <= 6 ? 6 : 16));
+}
 
 void vpass_plan(VArgs &a, int W, int H, int sh) {
     a.nw_ext = (W >> 5) + 1;

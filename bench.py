@@ -175,6 +175,39 @@ def alg_bytes(job_path, runs_in, runs_out_per_op):
     return 2 * page + 4 * (2 * runs_in + 2 * runs_out_per_op) + 4 * 4 * (H + 1)
 
 
+def csrc_digest():
+    """SHA-256 over the CUDA sources and the ABI header (ties a profile
+    record to the kernels it was taken from)."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_0712_0121_gb300", "csrc", "*.cu*")))
+    files.append(os.path.join(ROOT, "include", "morph.h"))
+    for f in files:
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode() + b"\0" + fh.read())
+    return h.hexdigest()
+
+
+def profile_traffic(name, pages):
+    """DRAM bytes per launch from a committed ncu record (profiles/<name>),
+    scaled to `pages` pages, or None when the record is missing or was taken
+    from other kernel sources."""
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and not line.startswith("|"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip().strip("-* `")] = v.strip().strip("`")
+        if kv.get("csrc_sha256") != csrc_digest():
+            return None
+        return int(float(kv["dram_bytes_per_launch"]) * pages / float(kv["pages"]))
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def time_launches(fn, steps, stream):
     import torch
     times = []
@@ -467,7 +500,8 @@ def run_ours(args):
         "pages_per_s": round(pages_per_s, 1),
         "packed_gpix_s": round(sub["packed"], 1), "rle_gpix_s": round(sub["rle"], 1),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": profile_traffic("k_batch_letter300_dram.md", B),
                      "kernel": "k_batch (persistent batch launch)", "peak_source": peak_src,
                      "alg_bytes_per_launch": int(bytes_launch)},
         "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d),

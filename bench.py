@@ -175,6 +175,24 @@ def alg_bytes(job_path, runs_in, runs_out_per_op):
     return 2 * page + 4 * (2 * runs_in + 2 * runs_out_per_op) + 4 * 4 * (H + 1)
 
 
+def max_over_ranks(x: float) -> float:
+    """Max of a float over the ranks of the default process group (the step
+    time every rank reports is the slowest rank's); identity on one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Units processed by all ranks per second, timed by the slowest rank."""
+    return units_per_rank * world / (ms_max * 1e-3)
+
+
 def csrc_digest():
     """SHA-256 over the CUDA sources and the ABI header (ties a profile
     record to the kernels it was taken from)."""
@@ -412,16 +430,12 @@ def run_ours(args):
     if st != M.MORPH_OK:
         raise RuntimeError("device status %d after the timed steps" % st)
     ms = statistics.mean(times)
-    ms_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = max_over_ranks(ms)
 
     n_jobs = len(jobs)
     pix_step_rank = n_jobs * W * H
-    value = pix_step_rank * world / (ms_max * 1e-3) / 1e9
-    pages_per_s = B * world / (ms_max * 1e-3)
+    value = whole_job_rate(pix_step_rank, world, ms_max) / 1e9
+    pages_per_s = whole_job_rate(B, world, ms_max)
 
     # algorithmic bytes per launch (run counts from the oracle-free device encode)
     rle_probe = M.Rle.empty(W, H, H * args.rle_runs_per_row)

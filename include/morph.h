@@ -87,7 +87,8 @@ typedef enum morph_op {
  *   packed: words (device, aligned to the word size), stride_words >=
  *           ceil(width / B) words of B bits between consecutive rows.
  *   RLE   : row_ptr (device int32[height+1], row_ptr[0] = 0), runs (device
- *           uint16[2*capacity_runs]), n_runs (device int64, may be NULL for
+ *           uint16[2*capacity_runs], aligned to 4 bytes: one (start, end)
+ *           pair), n_runs (device int64, may be NULL for
  *           inputs).  As an OUTPUT, the producer writes row_ptr, the runs and
  *           *n_runs = total runs needed; if that exceeds capacity_runs the runs
  *           are not written and MORPH_ECAPACITY is latched (row_ptr and *n_runs

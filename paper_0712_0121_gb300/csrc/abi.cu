@@ -65,6 +65,8 @@ morph_status check_image(const morph_image *im, const char *name) {
         if (!im->row_ptr) return fail(MORPH_EINVAL, "%s.row_ptr is NULL", name);
         if (im->capacity_runs < 0) return fail(MORPH_EINVAL, "%s.capacity_runs < 0", name);
         if (im->capacity_runs > 0 && !im->runs) return fail(MORPH_EINVAL, "%s.runs is NULL", name);
+        if ((uintptr_t)im->runs % 4)
+            return fail(MORPH_EINVAL, "%s.runs is not aligned to 4 bytes (one (start, end) pair)", name);
         return MORPH_OK;
     }
     return fail(MORPH_EINVAL, "%s.fmt %d is not a morph_format", name, im->fmt);

@@ -5,8 +5,8 @@
 // job is one phase of independent tiles (the fused tile of packed_tile.cuh).
 // An RLE job is a chain of phases — bitmap->RLE count, scan, write; per
 // erosion stage the run pass (count, scan, write) or the between-line pass
-// (rows to a bitmap with run counts, scan, encode; the last stage's rows go
-// straight to the job's packed output); RLE->bitmap after a run-pass stage —
+// (rows to a bitmap, run counts of the rows, scan, encode; the last stage's
+// rows go straight to the job's packed output); RLE->bitmap after a run-pass stage —
 // whose items depend on every item of the job's previous phase.
 // Items are listed by level (a job's phase index, shifted past the phases of
 // the job it depends on) and claimed in list order from a device queue by
@@ -41,7 +41,8 @@ enum ItemKind : int {
     IK_B2R_WRITE,
     IK_ROW_COUNT,
     IK_ROW_WRITE,
-    IK_V_BMP,      // between-line pass: rows to a bitmap (+ run counts if not the last stage)
+    IK_V_BMP,      // between-line pass: rows to a bitmap
+    IK_BCOUNT,     // run counts of the stored bitmap rows
     IK_BWRITE,     // encode the stored bitmap rows into runs
     IK_R2B,
     IK_OUT_SCAN,   // MORPH_TO_RLE: scan into the caller's RLE dst
@@ -159,6 +160,11 @@ __device__ __noinline__ void vpass_fn(const VArgs &a, int bx, uint32_t *sm) {
     vpass_tile<NWT, KMAX>(a, bx, sm);
 }
 
+template <int KMAX>
+__device__ __noinline__ void vband_fn(const VArgs &a, int bx, uint32_t *sm) {
+    vband_tile<2, KMAX>(a, bx, sm);
+}
+
 __device__ void run_vpass(int vkind, const VArgs &a, int bx, uint32_t *sm) {
     switch (vkind) {
     case 0: vpass_fn<2, 2>(a, bx, sm); break;
@@ -168,7 +174,11 @@ __device__ void run_vpass(int vkind, const VArgs &a, int bx, uint32_t *sm) {
     case 4: vpass_fn<8, 2>(a, bx, sm); break;
     case 5: vpass_fn<8, 3>(a, bx, sm); break;
     case 6: vpass_fn<8, 6>(a, bx, sm); break;
-    default: vpass_fn<8, 16>(a, bx, sm); break;
+    case 7: vpass_fn<8, 16>(a, bx, sm); break;
+    case 8: vband_fn<2>(a, bx, sm); break;
+    case 9: vband_fn<3>(a, bx, sm); break;
+    case 10: vband_fn<6>(a, bx, sm); break;
+    default: vband_fn<16>(a, bx, sm); break;
     }
 }
 
@@ -281,9 +291,16 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batch(const uint8_t *plan,
                 va.bmp = reinterpret_cast<uint32_t *>(ws + J.off_bmp);
                 va.bmp_stride = (J.W + 31) / 32;
                 va.bmp_words = (J.W + 31) / 32;
-                va.counts = reinterpret_cast<int32_t *>(ws + J.off_counts);
+                va.counts = nullptr;
             }
             run_vpass(J.vkind[st], va, it.idx, sm);
+            break;
+        }
+        case IK_BCOUNT: {
+            if (ovf) break;
+            const int r0 = it.idx * RLE_ROWS_PER_ITEM;
+            b2r_count_rows(reinterpret_cast<const uint32_t *>(ws + J.off_bmp), (J.W + 31) / 32, J.W, r0,
+                           min(J.H, r0 + RLE_ROWS_PER_ITEM), reinterpret_cast<int32_t *>(ws + J.off_counts));
             break;
         }
         case IK_BWRITE: {
@@ -393,7 +410,8 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
                 return berr(MORPH_EINVAL, "bad or different sizes (RLE width <= 65535)", j);
             const int Bs = s.fmt == MORPH_PACKED32 ? 32 : 64;
             if (!s.words || s.stride_words < (s.width + Bs - 1) / Bs || (uintptr_t)s.words % (Bs / 8) ||
-                !d.row_ptr || d.capacity_runs < 0 || (d.capacity_runs > 0 && !d.runs) || s.reserved || d.reserved)
+                !d.row_ptr || d.capacity_runs < 0 || (d.capacity_runs > 0 && !d.runs) || (uintptr_t)d.runs % 4 ||
+                s.reserved || d.reserved)
                 return berr(MORPH_EINVAL, "bad descriptor", j);
             b.path = -1;
             b.src = (const uint32_t *)s.words;
@@ -511,17 +529,27 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
                     v.ey = dil ? c.sh - 1 - c.oy : c.oy;
                     v.K = bitlen(c.sh);
                     for (int k = 0; k < 16; ++k) v.eqm[k] = ((c.sh >> k) & 1) ? 0u : ONES;
-                    vpass_plan(v, W, H, c.sh);
-                    v.capacity = b.cap;
                     const int km = vpass_kmax(c.sh);
-                    b.vkind[st] = (v.nwt == 2 ? 0 : 4) + (km == 2 ? 0 : (km == 3 ? 1 : (km == 6 ? 2 : 3)));
-                    const int sb = (int)vpass_smem_bytes(v);
+                    const int kk = km == 2 ? 0 : (km == 3 ? 1 : (km == 6 ? 2 : 3));
+                    int sb, grid;
+                    if (vband_plan(v, W, H, c.sh, VBAND_SMEM_BUDGET)) {
+                        b.vkind[st] = 8 + kk;
+                        sb = (int)vband_smem_bytes(v);
+                        grid = vband_grid(v);
+                    } else {
+                        vpass_plan(v, W, H, c.sh);
+                        b.vkind[st] = (v.nwt == 2 ? 0 : 4) + kk;
+                        sb = (int)vpass_smem_bytes(v);
+                        grid = vpass_grid(v);
+                    }
+                    v.capacity = b.cap;
                     if (sb > smem) smem = sb;
                     // rows -> bitmap; an intermediate stage is then encoded
                     // into runs (its run pass input for the next stage), the
                     // last stage's bitmap is the job's output
-                    add(IK_V_BMP, vpass_grid(v), st);
+                    add(IK_V_BMP, grid, st);
                     if (st < b.nst - 1) {
+                        add(IK_BCOUNT, rows_items, st);
                         add(IK_SCAN, 1, st);
                         add(IK_BWRITE, rows_items, st);
                     }

@@ -135,6 +135,14 @@ struct VArgs {
 // H and window height sh (block size up to MAX_THREADS).
 void vpass_plan(VArgs &a, int W, int H, int sh);
 size_t vpass_smem_bytes(const VArgs &a);
+// Band-tile variant (bitmap output only): tiling for a shared-memory budget;
+// false if one tile cannot hold the rows it needs (then use vpass_plan).
+bool vband_plan(VArgs &a, int W, int H, int sh, size_t smem_budget);
+size_t vband_smem_bytes(const VArgs &a);
+int vband_grid(const VArgs &a);
+constexpr size_t VBAND_SMEM_BUDGET = 96 * 1024;
+// Runs per staging buffer of the band tile (two buffers).
+constexpr int VBAND_RUN_CHUNK = 2048;
 int vpass_threads(const VArgs &a);
 int vpass_grid(const VArgs &a);
 int vpass_kmax(int sh);  // counter width for a window of sh rows

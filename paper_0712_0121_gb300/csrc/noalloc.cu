@@ -95,6 +95,8 @@ extern "C" morph_status morph_rle_rect_noalloc(int op, const morph_image *dst,
     if (!src->row_ptr || !dst->row_ptr || dst->capacity_runs < 0 || src->capacity_runs < 0 ||
         (dst->capacity_runs > 0 && !dst->runs))
         return reject(MORPH_EINVAL, "NULL row_ptr or runs, or negative capacity");
+    if ((uintptr_t)src->runs % 4 || (uintptr_t)dst->runs % 4)
+        return reject(MORPH_EINVAL, "runs must be aligned to 4 bytes (one (start, end) pair)");
     if (se_w < 1 || se_h < 1 || se_w > 65535 || se_h > 65535 || origin_x < 0 || origin_x >= se_w ||
         origin_y < 0 || origin_y >= se_h)
         return reject(MORPH_EINVAL, "bad structuring element %d x %d, origin (%d, %d)", se_w, se_h,

@@ -257,18 +257,20 @@ __device__ __forceinline__ void packed_tile(const PackedArgs &a, int bx, int by,
     const uint32_t inm_in = inv_in ? ONES : 0u, inm_out = inv_out ? ONES : 0u;
     const uint32_t nvm0 = ~vmask[0], nvm1 = ~vmask[1];
 
-    // Raw words of input row r (0 outside the image).
+    // Raw words of input row r (0 outside the image).  Plain loads: in the
+    // batch kernel a job's input can be another job's output written earlier
+    // in the same launch, which the read-only path may not see.
     auto load_raw = [&](int r, uint32_t (&raw)[NWT]) {
         raw[0] = raw[1] = 0u;
         if (r >= 0 && r < H && any_ld) {
             const uint32_t *p = src + (int64_t)r * sstride;
             if (vec_ld) {
-                const uint2 x = __ldg(reinterpret_cast<const uint2 *>(p));
+                const uint2 x = *reinterpret_cast<const uint2 *>(p);
                 raw[0] = x.x;
                 raw[1] = x.y;
             } else {
-                if (vmask[0]) raw[0] = __ldg(p);
-                if (vmask[1]) raw[1] = __ldg(p + 1);
+                if (vmask[0]) raw[0] = p[0];
+                if (vmask[1]) raw[1] = p[1];
             }
         }
     };

@@ -24,6 +24,19 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
+// Asynchronous 4-byte global -> shared copy (no register round trip); the
+// copies a thread issued complete at cp_async_wait<n> (all but its n most
+// recent groups), and become visible to the CTA after a barrier.
+__device__ __forceinline__ void cp_async4(uint32_t *sdst, const uint32_t *gsrc) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ int warp_excl_scan(int v, int lane, int &total) {
     int x = v;
 #pragma unroll
@@ -35,30 +48,59 @@ __device__ __forceinline__ int warp_excl_scan(int v, int lane, int &total) {
     return x - v;
 }
 
-// Word k of a packed row with padding bits cleared; 0 outside the row.
-__device__ __forceinline__ uint32_t row_word(const uint32_t *row, int k, int nw_valid, int W) {
-    return (k >= 0 && k < nw_valid) ? (__ldg(row + k) & word_mask(k, W)) : 0u;
-}
-
 // ------------------------------------------------------ bitmap -> RLE (K6)
 // Transition word k: bit b set iff pixel 32k+b differs from pixel 32k+b-1
 // (pixel -1 and pixels >= W are 0).  Words 0 .. W/32 cover positions 0..W.
-// One warp per row; rows [r0, r1).
+// Rows [r0, r1); a warp takes B2R_RPW rows at once (rows warp, warp+nwarps,
+// ...) and issues the loads of all of them before using any, so one memory
+// round trip serves B2R_RPW rows.  Word k-1's top bit comes from lane k-1
+// (lane 0: the previous chunk's lane 31).  Plain loads, not the read-only
+// path: in the batch kernel the bitmap may have been written earlier in the
+// same launch.
+constexpr int B2R_RPW = 8;
+
+__device__ __forceinline__ void b2r_load(const uint32_t *src, int64_t sstride, int W, int nw_valid,
+                                         int yb, int ystep, int r1, int k,
+                                         uint32_t (&w)[B2R_RPW]) {
+    const bool kin = k < nw_valid;
+    const uint32_t m = kin ? word_mask(k, W) : 0u;
+#pragma unroll
+    for (int j = 0; j < B2R_RPW; ++j) {
+        const int y = yb + j * ystep;
+        w[j] = (kin && y < r1) ? (src[(int64_t)y * sstride + k] & m) : 0u;
+    }
+}
+
+__device__ __forceinline__ uint32_t b2r_trans(uint32_t w, uint32_t &carry, int lane) {
+    uint32_t p = __shfl_up_sync(FULL_MASK, w, 1);
+    if (lane == 0) p = carry;
+    carry = __shfl_sync(FULL_MASK, w, 31);
+    return w ^ ((w << 1) | (p >> 31));
+}
+
 __device__ __forceinline__ void b2r_count_rows(const uint32_t *src, int64_t sstride, int W, int r0,
                                                int r1, int32_t *counts) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int nw_valid = (W + 31) >> 5, nw_ext = (W >> 5) + 1;
-    for (int y = r0 + warp; y < r1; y += nwarps) {
-        const uint32_t *row = src + (int64_t)y * sstride;
-        int cnt = 0;
-        for (int k = lane; k < nw_ext; k += 32) {
-            const uint32_t w = row_word(row, k, nw_valid, W);
-            const uint32_t p = row_word(row, k - 1, nw_valid, W);
-            cnt += __popc(w ^ ((w << 1) | (p >> 31)));
+    for (int yb = r0 + warp; yb < r1; yb += nwarps * B2R_RPW) {
+        int cnt[B2R_RPW];
+        uint32_t carry[B2R_RPW];
+#pragma unroll
+        for (int j = 0; j < B2R_RPW; ++j) cnt[j] = 0, carry[j] = 0u;
+        for (int k0 = 0; k0 < nw_ext; k0 += 32) {
+            uint32_t w[B2R_RPW];
+            b2r_load(src, sstride, W, nw_valid, yb, nwarps, r1, k0 + lane, w);
+#pragma unroll
+            for (int j = 0; j < B2R_RPW; ++j) cnt[j] += __popc(b2r_trans(w[j], carry[j], lane));
         }
 #pragma unroll
-        for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(FULL_MASK, cnt, o);
-        if (lane == 0) counts[y] = cnt >> 1;
+        for (int j = 0; j < B2R_RPW; ++j) {
+            int c = cnt[j];
+#pragma unroll
+            for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(FULL_MASK, c, o);
+            const int y = yb + j * nwarps;
+            if (lane == 0 && y < r1) counts[y] = c >> 1;
+        }
     }
 }
 
@@ -66,48 +108,74 @@ __device__ __forceinline__ void b2r_write_rows(const uint32_t *src, int64_t sstr
                                                int r1, const int32_t *row_ptr, uint16_t *runs) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int nw_valid = (W + 31) >> 5, nw_ext = (W >> 5) + 1;
-    for (int y = r0 + warp; y < r1; y += nwarps) {
-        const uint32_t *row = src + (int64_t)y * sstride;
-        int64_t pos0 = 2 * (int64_t)row_ptr[y];
+    for (int yb = r0 + warp; yb < r1; yb += nwarps * B2R_RPW) {
+        int64_t pos[B2R_RPW];
+        uint32_t carry[B2R_RPW];
+#pragma unroll
+        for (int j = 0; j < B2R_RPW; ++j) {
+            const int y = yb + j * nwarps;
+            pos[j] = y < r1 ? 2 * (int64_t)row_ptr[y] : 0;
+            carry[j] = 0u;
+        }
         for (int k0 = 0; k0 < nw_ext; k0 += 32) {
             const int k = k0 + lane;
-            uint32_t t = 0;
-            if (k < nw_ext) {
-                const uint32_t w = row_word(row, k, nw_valid, W);
-                const uint32_t p = row_word(row, k - 1, nw_valid, W);
-                t = w ^ ((w << 1) | (p >> 31));
+            uint32_t w[B2R_RPW], t[B2R_RPW];
+            int ex[B2R_RPW], tot[B2R_RPW];
+            b2r_load(src, sstride, W, nw_valid, yb, nwarps, r1, k, w);
+            // the rows' transition words and offsets first (independent, so
+            // their shuffle chains overlap), then the data-dependent stores;
+            // lanes past word W/32 see w == 0 after a top bit of 0: t == 0
+#pragma unroll
+            for (int j = 0; j < B2R_RPW; ++j) t[j] = b2r_trans(w[j], carry[j], lane);
+#pragma unroll
+            for (int j = 0; j < B2R_RPW; ++j) ex[j] = __popc(t[j]);
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+                for (int j = 0; j < B2R_RPW; ++j) {
+                    const int y = __shfl_up_sync(FULL_MASK, ex[j], o);
+                    if (lane >= o) ex[j] += y;
+                }
             }
-            int tot;
-            const int ex = warp_excl_scan(__popc(t), lane, tot);
-            int64_t pos = pos0 + ex;
-            while (t) {
-                const int b = __ffs(t) - 1;
-                runs[pos++] = (uint16_t)(32 * k + b);
-                t &= t - 1;
+#pragma unroll
+            for (int j = 0; j < B2R_RPW; ++j) {
+                tot[j] = __shfl_sync(FULL_MASK, ex[j], 31);
+                ex[j] -= __popc(t[j]);
             }
-            pos0 += tot;
+#pragma unroll
+            for (int j = 0; j < B2R_RPW; ++j) {
+                uint32_t tj = t[j];
+                int64_t q = pos[j] + ex[j];
+                while (tj) {
+                    const int b = __ffs(tj) - 1;
+                    runs[q++] = (uint16_t)(32 * k + b);
+                    tj &= tj - 1;
+                }
+                pos[j] += tot[j];
+            }
         }
     }
 }
 
-// Exclusive prefix sum of counts[0..H) into row_ptr[0..H], the total into
-// row_ptr[H] and *n_runs; latches MORPH_ECAPACITY when total > capacity.
-// One CTA (any size that is a multiple of 32, up to 1024).
-__device__ __forceinline__ void scan_rows_block(const int32_t *counts, int H, int32_t *row_ptr,
-                                                int64_t *n_runs, int64_t capacity, int *status) {
+// Exclusive prefix sum, by one CTA (any size that is a multiple of 32, up to
+// 1024), of in[0], in[istride], ... (n values) plus `base` into out[0],
+// out[ostride], ...; returns base + the sum to every thread.  Every read of
+// a pass happens before its writes, so in == out works in place.
+__device__ __forceinline__ int64_t scan_block(const int32_t *in, int64_t istride, int n,
+                                              int32_t *out, int64_t ostride, int64_t base0) {
     constexpr int ITEMS = 4;
     __shared__ int64_t wsum[32];
     __shared__ int64_t base_s;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int nthreads = blockDim.x;
-    if (tid == 0) base_s = 0;
+    if (tid == 0) base_s = base0;
     __syncthreads();
-    for (int start = 0; start < H; start += nthreads * ITEMS) {
+    for (int start = 0; start < n; start += nthreads * ITEMS) {
         int64_t v[ITEMS], loc = 0;
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
             const int idx = start + tid * ITEMS + j;
-            v[j] = idx < H ? counts[idx] : 0;
+            v[j] = idx < n ? in[idx * istride] : 0;
             loc += v[j];
         }
         int64_t x = loc;
@@ -133,15 +201,25 @@ __device__ __forceinline__ void scan_rows_block(const int32_t *counts, int H, in
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
             const int idx = start + tid * ITEMS + j;
-            if (idx < H) row_ptr[idx] = (int32_t)run;
+            if (idx < n) out[idx * ostride] = (int32_t)run;
             run += v[j];
         }
         __syncthreads();
         if (tid == 0) base_s = base + wsum[nwarps - 1];
         __syncthreads();
     }
-    if (tid == 0) {
-        const int64_t total = base_s;
+    const int64_t total = base_s;
+    __syncthreads();  // base_s is reused by the next call
+    return total;
+}
+
+// Exclusive prefix sum of counts[0..H) into row_ptr[0..H], the total into
+// row_ptr[H] and *n_runs; latches MORPH_ECAPACITY when total > capacity.
+// One CTA (any size that is a multiple of 32, up to 1024).
+__device__ __forceinline__ void scan_rows_block(const int32_t *counts, int H, int32_t *row_ptr,
+                                                int64_t *n_runs, int64_t capacity, int *status) {
+    const int64_t total = scan_block(counts, 1, H, row_ptr, 1, 0);
+    if (threadIdx.x == 0) {
         row_ptr[H] = (int32_t)total;
         if (n_runs) *n_runs = total;
         if (total > capacity) latch_status(status, MORPH_ECAPACITY);
@@ -212,6 +290,35 @@ __device__ __forceinline__ RunT row_op(const uint16_t *runs, int64_t i, int64_t 
         r.ke = (i == b - 1) || ((int)runs[2 * i + 2] - e > op.sw - 1);
     }
     return r;
+}
+
+// The run [s, e) after the row pass, as an interval (empty when s2 >= e2).
+// Dilated runs may overlap their neighbours: painting them with OR merges
+// them, so no neighbour test is needed where the result is a bitmap row.
+__device__ __forceinline__ void run_interval(uint32_t pair, const RowOp &op, int &s2, int &e2) {
+    const int s = (int)(pair & 0xFFFFu), e = (int)(pair >> 16);
+    if (!op.dilate) {
+        s2 = (s == 0) ? 0 : s + op.o;
+        e2 = (e >= op.W) ? op.W : e - (op.sw - 1 - op.o);
+    } else {
+        s2 = s - op.o < 0 ? 0 : s - op.o;
+        e2 = e + op.sw - 1 - op.o > op.W ? op.W : e + op.sw - 1 - op.o;
+    }
+}
+
+// OR the pixels [s, e) (0 <= s < e) into a shared-memory row.  The partial
+// end words are shared with other runs (atomic OR); the words in between
+// belong to this run alone, or end up all ones whatever the order.
+__device__ __forceinline__ void paint_run(uint32_t *rowp, int s, int e) {
+    const int ws = s >> 5, we = (e - 1) >> 5;
+    const uint32_t ms = ONES << (s & 31), me = ONES >> (31 - ((e - 1) & 31));
+    if (ws == we) {
+        atomicOr(rowp + ws, ms & me);
+    } else {
+        atomicOr(rowp + ws, ms);
+        for (int w = ws + 1; w < we; ++w) rowp[w] = ONES;
+        atomicOr(rowp + we, me);
+    }
 }
 
 // One warp per row; rows [r0, r1).  Count pass (write == 0) or write pass.
@@ -424,6 +531,157 @@ __device__ __forceinline__ void vpass_tile(const VArgs &a, int bx, uint32_t *sm)
         }
     }
     __syncthreads();
+}
+
+// Band tile of the between-line pass (bitmap output).  A tile owns the
+// output rows [Y0, Y0 + groups*band); every input row it needs (those rows
+// shifted by -ey, plus sh-1 more) is built ONCE as pixels in shared memory:
+//   P1 clear the rows and read each row's run offset; P2 stage the tile's
+//   runs (one contiguous range of the run array) chunk by chunk, double
+//   buffered with asynchronous copies, and paint
+//   every run, after the within-line pass, into its row with OR — the union
+//   of the row's intervals, overlapping dilated runs included;
+//   P4 each thread walks its words down one of `groups` segments of the band
+//   (a segment starts sh-1 rows early to warm its counters) reading the rows
+//   from shared memory, and stores every output word straight to the bitmap.
+// Two barriers per run chunk, none per row.  sm: vband_smem_bytes().
+template <int NWT, int KMAX>
+__device__ __forceinline__ void vband_tile(const VArgs &a, int bx, uint32_t *sm) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int g = tid / a.tpr, lt = tid - g * a.tpr;
+    const bool act = g < a.groups;
+    const int W = a.in.W, H = a.in.H;
+    const int nw_valid = (W + 31) >> 5;
+    const int stride = a.slot_words;               // words per tile row (>= nw_ext)
+    const int S = a.band, sh = a.sh;
+    const int Y0 = bx * a.groups * S;              // first output row of the tile
+    const int R = a.groups * S + sh - 1;           // tile rows
+    const int r0 = Y0 - a.ey;                      // input row of tile row 0
+    uint32_t *T = sm;
+    int *sP = reinterpret_cast<int *>(T + (size_t)R * stride);
+    uint32_t *sR = T + ((((size_t)R * stride + R + 1) * 4 + 15) & ~(size_t)15) / 4;
+    const uint32_t *runs32 = reinterpret_cast<const uint32_t *>(a.in.runs);
+
+    // P1: clear the rows; sP[i] = index of the first run of tile row i (rows
+    // outside the image have none: their offsets clamp to rows 0 and H)
+    {
+        const int n = R * stride, n4 = n >> 2;
+        uint4 *T4 = reinterpret_cast<uint4 *>(T);
+        for (int q = tid; q < n4; q += blockDim.x) T4[q] = make_uint4(0u, 0u, 0u, 0u);
+        for (int q = 4 * n4 + tid; q < n; q += blockDim.x) T[q] = 0u;
+    }
+    for (int i = tid; i <= R; i += blockDim.x) {
+        const int r = min(max(r0 + i, 0), H);
+        sP[i] = a.in.row_ptr[r];
+    }
+    __syncthreads();
+    // P2: the tile's runs are one contiguous range of the run array.  Stage
+    // it chunk by chunk with asynchronous copies into two buffers (chunk c+1
+    // is in flight while chunk c is painted) and paint every run, after the
+    // row pass, into its row
+    {
+        const int qb = sP[0], qe = sP[R];
+        const int nch = (qe - qb + VBAND_RUN_CHUNK - 1) / VBAND_RUN_CHUNK;
+        auto issue = [&](int c) {
+            const int c0 = qb + c * VBAND_RUN_CHUNK, ns = min(qe - c0, VBAND_RUN_CHUNK);
+            uint32_t *buf = sR + (c & 1) * VBAND_RUN_CHUNK;
+            for (int k = tid; k < ns; k += blockDim.x) cp_async4(buf + k, runs32 + c0 + k);
+            cp_async_commit();
+        };
+        if (nch > 0) issue(0);
+        for (int c = 0; c < nch; ++c) {
+            if (c + 1 < nch) {
+                issue(c + 1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncthreads();
+            const int c0 = qb + c * VBAND_RUN_CHUNK, c1 = min(qe, c0 + VBAND_RUN_CHUNK);
+            const uint32_t *buf = sR + (c & 1) * VBAND_RUN_CHUNK;
+            // each warp paints a contiguous share of the chunk's runs; a
+            // lane finds its run's row by walking forward from the row of
+            // the warp's previous 32 runs (empty rows are skipped)
+            const int per = ((c1 - c0 + nwarps - 1) / nwarps + 31) & ~31;
+            const int w0 = c0 + warp * per, w1 = min(c1, w0 + per);
+            if (w0 < w1) {
+                int lo = 0, hi = R;  // sP[lo] <= w0 < sP[hi]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (sP[mid] <= w0) lo = mid;
+                    else hi = mid;
+                }
+                int r = lo;
+                for (int q0 = w0; q0 < w1; q0 += 32) {
+                    const int q = min(q0 + lane, w1 - 1);
+                    int rr = r;
+                    while (sP[rr + 1] <= q) ++rr;
+                    if (q0 + lane < w1) {
+                        int s2, e2;
+                        run_interval(buf[q - c0], a.op, s2, e2);
+                        // the clamps only matter for a non-canonical input list
+                        s2 = max(s2, 0);
+                        e2 = min(e2, W);
+                        if (s2 < e2) paint_run(T + (size_t)rr * stride, s2, e2);
+                    }
+                    r = __shfl_sync(FULL_MASK, rr, 31);
+                }
+            }
+            __syncthreads();  // buffer c & 1 is refilled by the next issue
+        }
+    }
+    // P4: column counters down each segment, output words straight to global
+    if (!act) return;
+    uint32_t vmask[NWT], eqm[KMAX];
+    bool st_ok[NWT];
+    ColCounter<KMAX> cc[NWT];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) eqm[k] = a.eqm[k];
+#pragma unroll
+    for (int t = 0; t < NWT; ++t) {
+        const int w = lt * NWT + t;
+        vmask[t] = w < nw_valid ? word_mask(w, W) : 0u;
+        st_ok[t] = w < a.bmp_words;
+        cc[t].reset();
+    }
+    const uint32_t invm = a.inv ? ONES : 0u;
+    const int i0 = g * S;                          // first tile row of the segment
+    // NWT == 2: one 64-bit shared load per row (rows start at even words) and
+    // one 64-bit store when the output rows allow it
+    const bool vec_st = NWT == 2 && st_ok[NWT - 1] && (a.bmp_stride & 1) == 0 &&
+                        ((uintptr_t)a.bmp & 7) == 0;
+    for (int it = 0; it < S + sh - 1; ++it) {
+        const int i = i0 + it;
+        const int r = r0 + i;
+        const bool rin = r >= 0 && r < H;
+        const uint32_t *tp = T + (size_t)i * stride + lt * NWT;
+        uint32_t x[NWT], o[NWT];
+        if constexpr (NWT == 2) {
+            const uint2 v2 = *reinterpret_cast<const uint2 *>(tp);
+            x[0] = v2.x;
+            x[1] = v2.y;
+        } else {
+#pragma unroll
+            for (int t = 0; t < NWT; ++t) x[t] = tp[t];
+        }
+#pragma unroll
+        for (int t = 0; t < NWT; ++t) {
+            const uint32_t v = rin ? ((x[t] ^ invm) | ~vmask[t]) : ONES;
+            o[t] = (cc[t].push(v, a.K, eqm) ^ invm) & vmask[t];
+        }
+        const int y = Y0 + i0 + it - (sh - 1);
+        if (it >= sh - 1 && y < H) {
+            uint32_t *p = a.bmp + (int64_t)y * a.bmp_stride + lt * NWT;
+            if (vec_st) {
+                *reinterpret_cast<uint2 *>(p) = make_uint2(o[0], o[NWT - 1]);
+            } else {
+#pragma unroll
+                for (int t = 0; t < NWT; ++t)
+                    if (st_ok[t]) p[t] = o[t];
+            }
+        }
+    }
 }
 
 }  // namespace morph

@@ -96,6 +96,9 @@ def test_rle_checks_and_workspace(M):
     assert _call(M, 0, rle(rp=0x1004, runs=0x6000), src) == M.MORPH_EINVAL  # row_ptr overlap
     mixed = _img(M, words=0x90000)
     assert _call(M, 0, mixed, src) == M.MORPH_EINVAL              # packed dst, RLE src
+    odd = rle(rp=0x5000, runs=0x6002)
+    assert _call(M, 0, odd, src, ws=0x900000, nws=need) == M.MORPH_EINVAL  # runs not 4-byte aligned
+    assert b"aligned" in M.lib().morph_last_error()
 
 
 def test_packed_workspace_only_for_wide_rectangles(M):

@@ -148,3 +148,23 @@ def test_config3_rle_full_page(kind):
     img, _ = synth.config3_page(kind)
     for op, sw, sh in (("dilate", 101, 1), ("dilate", 1, 61), ("open", 5, 5)):
         check_rle(op, img, sw, sh, sw // 2, sh // 2, mode="separable")
+
+
+@pytest.mark.parametrize("H", [8192, 8193, 12289, 70001])
+def test_tall_images_multi_cta_scan(H):
+    # above 8192 rows the row offsets come from the multi-CTA scan: segment
+    # boundaries, a ragged last segment and many segments
+    img = synth.random_bits((H, 130), 5000 + H, 0.7)
+    rle = to_rle(img)
+    rp, runs = oracle.rle_encode(img)
+    assert_rle_equal(rle, rp, runs)
+    for op in ("erode", "close"):
+        check_rle(op, img, 5, 3, 2, 1, mode="separable")
+
+
+def test_tall_capacity_overflow():
+    img = synth.random_bits((20000, 100), 43, 0.5)
+    ref = oracle.rle_encode(oracle.dilate(img, 1, 3))[1].shape[0]
+    dst, st = rle_op("dilate", img, 1, 3, 0, 1, capacity=ref - 1)
+    assert st == M.MORPH_ECAPACITY
+    assert int(dst.n_runs.item()) == ref

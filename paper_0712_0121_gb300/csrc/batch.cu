@@ -191,7 +191,7 @@ struct Ctrl {
 __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batch(const uint8_t *plan, uint8_t *ws,
                                                            int *status) {
     extern __shared__ __align__(16) uint32_t sm[];
-    __shared__ int s_item, s_ok;
+    __shared__ int s_next[2], s_ok;
     const BatchHeader *hdr = reinterpret_cast<const BatchHeader *>(plan);
     const BatchJob *jobs = reinterpret_cast<const BatchJob *>(plan + hdr->jobs_off);
     const BatchItem *items = reinterpret_cast<const BatchItem *>(plan + hdr->items_off);
@@ -200,15 +200,20 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batch(const uint8_t *plan,
     int *overflow = done + (size_t)hdr->n_jobs * MAX_PH;
     const int n_items = hdr->n_items;
 
-    for (;;) {
-        if (threadIdx.x == 0) {
-            s_item = *(volatile int *)&ctrl->abort_flag ? n_items : atomicAdd(&ctrl->head, 1);
-        }
-        __syncthreads();
-        const int i = s_item;
+    // Thread 0 reserves the CTA's next item as soon as the current one may
+    // start, and publishes it when the current one ends: the queue atomic's
+    // latency hides behind the work.  A CTA holds at most one reserved item
+    // besides the one it runs, and items are reserved in list (level)
+    // order, so the lowest unfinished item can always proceed.
+    if (threadIdx.x == 0)
+        s_next[0] = *(volatile int *)&ctrl->abort_flag ? n_items : atomicAdd(&ctrl->head, 1);
+    __syncthreads();
+    for (int k = 0;; ++k) {
+        const int i = s_next[k & 1];
         if (i >= n_items) break;
         const BatchItem it = items[i];
         const BatchJob &J = jobs[it.job];
+        int nxt = n_items;
         if (threadIdx.x == 0) {
             bool ok = true;
             if (it.phase > 0) {
@@ -222,6 +227,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batch(const uint8_t *plan,
                                 (unsigned long long)hdr->wait_limit_ns);
             }
             s_ok = ok;
+            if (ok && !*(volatile int *)&ctrl->abort_flag) nxt = atomicAdd(&ctrl->head, 1);
         }
         __syncthreads();
         if (!s_ok) break;
@@ -241,7 +247,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batch(const uint8_t *plan,
         case IK_B2R_WRITE: {
             if (ovf) break;
             const int r0 = it.idx * RLE_ROWS_PER_ITEM;
-            b2r_write_rows(J.src, J.sstride, J.W, r0, min(J.H, r0 + RLE_ROWS_PER_ITEM),
+            b2r_write_rows<3>(J.src, J.sstride, J.W, r0, min(J.H, r0 + RLE_ROWS_PER_ITEM),
                            reinterpret_cast<const int32_t *>(ws + J.off_rpA),
                            reinterpret_cast<uint16_t *>(ws + J.off_runsA));
             break;
@@ -306,7 +312,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batch(const uint8_t *plan,
         case IK_BWRITE: {
             if (ovf) break;
             const int r0 = it.idx * RLE_ROWS_PER_ITEM;
-            b2r_write_rows(reinterpret_cast<const uint32_t *>(ws + J.off_bmp), (J.W + 31) / 32, J.W, r0,
+            b2r_write_rows<3>(reinterpret_cast<const uint32_t *>(ws + J.off_bmp), (J.W + 31) / 32, J.W, r0,
                            min(J.H, r0 + RLE_ROWS_PER_ITEM),
                            reinterpret_cast<const int32_t *>(ws + J.off_rpB),
                            reinterpret_cast<uint16_t *>(ws + J.off_runsB));
@@ -321,7 +327,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batch(const uint8_t *plan,
         case IK_OUT_WRITE: {
             if (ovf) break;
             const int r0 = it.idx * RLE_ROWS_PER_ITEM;
-            b2r_write_rows(J.src, J.sstride, J.W, r0, min(J.H, r0 + RLE_ROWS_PER_ITEM),
+            b2r_write_rows<3>(J.src, J.sstride, J.W, r0, min(J.H, r0 + RLE_ROWS_PER_ITEM),
                            J.out.row_ptr, J.out.runs);
             break;
         }
@@ -339,6 +345,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batch(const uint8_t *plan,
             break;
         }
         __threadfence();
+        if (threadIdx.x == 0) s_next[(k + 1) & 1] = nxt;
         __syncthreads();
         if (threadIdx.x == 0) atomicAdd(done + (size_t)it.job * MAX_PH + it.phase, 1);
     }

@@ -19,7 +19,7 @@ __global__ void __launch_bounds__(256, 3) k_b2r_write(const uint32_t *src, int64
                                                    uint16_t *runs) {
     if ((int64_t)row_ptr[H] > capacity) return;
     for (int r0 = blockIdx.x * RLE_ROWS_PER_ITEM; r0 < H; r0 += gridDim.x * RLE_ROWS_PER_ITEM)
-        b2r_write_rows(src, sstride, W, r0, min(H, r0 + RLE_ROWS_PER_ITEM), row_ptr, runs);
+        b2r_write_rows<1>(src, sstride, W, r0, min(H, r0 + RLE_ROWS_PER_ITEM), row_ptr, runs);
 }
 
 __global__ void __launch_bounds__(1024) k_scan_rows(const int32_t *counts, int H, int32_t *row_ptr,

@@ -214,8 +214,10 @@ MORPH_API morph_status rle_to_bitmap(const morph_image *dst_packed, const morph_
  * than the plan's limit (4 s) latches MORPH_ETIMEOUT and stops every CTA; an RLE buffer that is
  * too small latches MORPH_ECAPACITY and leaves that job's dst unwritten.
  *
- * tile_rows: row-band height of packed tiles for jobs whose own tile_rows is
- * 0 (0 = library default).
+ * tile_rows: for jobs whose own tile_rows is 0, the row-band height of
+ * packed tiles and the rows per work item of RLE-path and MORPH_TO_RLE jobs
+ * (0 = library defaults; RLE items hold a multiple of 64 rows, at most 1024,
+ * by default more the more RLE rows the plan holds).
  * rle_runs_per_row: room per row in each RLE buffer of RLE-path jobs
  * (0 = W/16 + 4, at most ceil(W/2)).
  * Limits: packed-path rectangles must reach <= 128 pixels left and right of
@@ -230,7 +232,8 @@ typedef struct morph_job {
     int32_t depends_on;  /* index of an EARLIER job of the plan whose work must
                             finish before this one starts (e.g. the job that
                             writes this job's src), or -1 */
-    int32_t tile_rows;   /* packed path: row-band height of its tiles (0 = the
+    int32_t tile_rows;   /* packed path: row-band height of its tiles; RLE path
+                            and MORPH_TO_RLE: rows per work item (0 = the
                             plan's tile_rows, else the library default) */
     morph_image src;     /* packed */
     morph_image dst;     /* packed, same size; RLE for MORPH_TO_RLE */

@@ -31,6 +31,12 @@ namespace {
 
 constexpr uint32_t PLAN_MAGIC = 0x4d425031u;  // "MBP1"
 constexpr int MAX_PH = 11;
+// Rows per row-range item (bitmap <-> runs, row pass, runs -> bitmap): a
+// multiple of 64 up to 1024, chosen per job at plan time.
+constexpr int BATCH_ROWS_MIN = 64, BATCH_ROWS_MAX = 1024;
+// Row-range items per phase that keep two CTAs on each of 152 SMs busy
+// several times over.
+constexpr int64_t ROW_ITEMS_TARGET = 8 * 2 * 152;
 constexpr int BATCH_THREADS = 256;
 constexpr long long WAIT_LIMIT_NS = 4000000000ll;  // default 4 s
 
@@ -72,6 +78,7 @@ struct BatchJob {
     int32_t vkind[2];           // between-line variant (nwt, kmax)
     int64_t off_counts, off_rpA, off_runsA, off_rpB, off_runsB, off_nA, off_nB, off_bmp;
     int64_t cap;                // runs capacity of each RLE buffer
+    int rows;                   // rows per row-range item
 };
 
 struct BatchItem {
@@ -239,15 +246,15 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batch(const uint8_t *plan,
             run_packed_tile(J.variant, J.pa, it.idx % J.gx, it.idx / J.gx, sm);
             break;
         case IK_B2R_COUNT: {
-            const int r0 = it.idx * RLE_ROWS_PER_ITEM;
-            b2r_count_rows(J.src, J.sstride, J.W, r0, min(J.H, r0 + RLE_ROWS_PER_ITEM),
+            const int r0 = it.idx * J.rows;
+            b2r_count_rows(J.src, J.sstride, J.W, r0, min(J.H, r0 + J.rows),
                            reinterpret_cast<int32_t *>(ws + J.off_counts));
             break;
         }
         case IK_B2R_WRITE: {
             if (ovf) break;
-            const int r0 = it.idx * RLE_ROWS_PER_ITEM;
-            b2r_write_rows<3>(J.src, J.sstride, J.W, r0, min(J.H, r0 + RLE_ROWS_PER_ITEM),
+            const int r0 = it.idx * J.rows;
+            b2r_write_rows<3>(J.src, J.sstride, J.W, r0, min(J.H, r0 + J.rows),
                            reinterpret_cast<const int32_t *>(ws + J.off_rpA),
                            reinterpret_cast<uint16_t *>(ws + J.off_runsA));
             break;
@@ -272,12 +279,12 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batch(const uint8_t *plan,
             const RleIn in{reinterpret_cast<const int32_t *>(ws + (fromA ? J.off_rpA : J.off_rpB)),
                            reinterpret_cast<const uint16_t *>(ws + (fromA ? J.off_runsA : J.off_runsB)),
                            J.W, J.H};
-            const int r0 = it.idx * RLE_ROWS_PER_ITEM;
+            const int r0 = it.idx * J.rows;
             const bool write = it.kind == IK_ROW_WRITE;
             rowpass_rows(in, J.rop[st], write, reinterpret_cast<int32_t *>(ws + J.off_counts),
                          reinterpret_cast<const int32_t *>(ws + (fromA ? J.off_rpB : J.off_rpA)),
                          reinterpret_cast<uint16_t *>(ws + (fromA ? J.off_runsB : J.off_runsA)), r0,
-                         min(J.H, r0 + RLE_ROWS_PER_ITEM));
+                         min(J.H, r0 + J.rows));
             break;
         }
         case IK_V_BMP: {
@@ -304,16 +311,16 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batch(const uint8_t *plan,
         }
         case IK_BCOUNT: {
             if (ovf) break;
-            const int r0 = it.idx * RLE_ROWS_PER_ITEM;
+            const int r0 = it.idx * J.rows;
             b2r_count_rows(reinterpret_cast<const uint32_t *>(ws + J.off_bmp), (J.W + 31) / 32, J.W, r0,
-                           min(J.H, r0 + RLE_ROWS_PER_ITEM), reinterpret_cast<int32_t *>(ws + J.off_counts));
+                           min(J.H, r0 + J.rows), reinterpret_cast<int32_t *>(ws + J.off_counts));
             break;
         }
         case IK_BWRITE: {
             if (ovf) break;
-            const int r0 = it.idx * RLE_ROWS_PER_ITEM;
+            const int r0 = it.idx * J.rows;
             b2r_write_rows<3>(reinterpret_cast<const uint32_t *>(ws + J.off_bmp), (J.W + 31) / 32, J.W, r0,
-                           min(J.H, r0 + RLE_ROWS_PER_ITEM),
+                           min(J.H, r0 + J.rows),
                            reinterpret_cast<const int32_t *>(ws + J.off_rpB),
                            reinterpret_cast<uint16_t *>(ws + J.off_runsB));
             break;
@@ -326,8 +333,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batch(const uint8_t *plan,
         }
         case IK_OUT_WRITE: {
             if (ovf) break;
-            const int r0 = it.idx * RLE_ROWS_PER_ITEM;
-            b2r_write_rows<3>(J.src, J.sstride, J.W, r0, min(J.H, r0 + RLE_ROWS_PER_ITEM),
+            const int r0 = it.idx * J.rows;
+            b2r_write_rows<3>(J.src, J.sstride, J.W, r0, min(J.H, r0 + J.rows),
                            J.out.row_ptr, J.out.runs);
             break;
         }
@@ -337,8 +344,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batch(const uint8_t *plan,
             const RleIn in{reinterpret_cast<const int32_t *>(ws + (fromA ? J.off_rpA : J.off_rpB)),
                            reinterpret_cast<const uint16_t *>(ws + (fromA ? J.off_runsA : J.off_runsB)),
                            J.W, J.H};
-            const int r0 = it.idx * RLE_ROWS_PER_ITEM;
-            r2b_rows(in, J.dst, J.dstride, J.nw_cover, r0, min(J.H, r0 + RLE_ROWS_PER_ITEM), sm);
+            const int r0 = it.idx * J.rows;
+            r2b_rows(in, J.dst, J.dstride, J.nw_cover, r0, min(J.H, r0 + J.rows), sm);
             break;
         }
         default:
@@ -399,6 +406,19 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
                    int64_t &ws_total, int &smem) {
     J.assign(n, BatchJob{});
     smem = 0;
+    // Default rows per row-range item: larger items amortise the per-item
+    // cost (claim, dependency check, job fields) once the plan has enough
+    // row-range work to keep every CTA busy with the larger items too.
+    int64_t rle_rows = 0;
+    for (int j = 0; j < n; ++j)
+        if (jobs[j].op == MORPH_TO_RLE || jobs[j].path == MORPH_PATH_RLE) rle_rows += jobs[j].src.height;
+    int auto_rows = BATCH_ROWS_MIN;
+    while (auto_rows < BATCH_ROWS_MAX && rle_rows / (2 * auto_rows) >= ROW_ITEMS_TARGET) auto_rows *= 2;
+    auto item_rows = [&](const morph_job &q) {
+        const int want = q.tile_rows ? q.tile_rows : (tile_rows ? tile_rows : auto_rows);
+        int r = (want + BATCH_ROWS_MIN - 1) / BATCH_ROWS_MIN * BATCH_ROWS_MIN;
+        return r > BATCH_ROWS_MAX ? BATCH_ROWS_MAX : r;
+    };
     int64_t off = al(sizeof(Ctrl) + (size_t)n * MAX_PH * sizeof(int) + (size_t)n * sizeof(int));
     ws_ctrl = off;
     for (int j = 0; j < n; ++j) {
@@ -428,7 +448,8 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
             b.out = RleOut{d.row_ptr, d.runs, d.capacity_runs, d.n_runs};
             b.off_counts = off;
             off += al((size_t)b.H * 4);
-            const int rows_items = (b.H + RLE_ROWS_PER_ITEM - 1) / RLE_ROWS_PER_ITEM;
+            b.rows = item_rows(q);
+            const int rows_items = (b.H + b.rows - 1) / b.rows;
             b.nphase = 3;
             b.phase_kind[0] = IK_B2R_COUNT; b.phase_items[0] = rows_items; b.phase_stage[0] = -1;
             b.phase_kind[1] = IK_OUT_SCAN;  b.phase_items[1] = 1;          b.phase_stage[1] = -1;
@@ -505,7 +526,8 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
                 b.off_bmp = off;
                 off += al((size_t)H * ((W + 31) / 32) * 4);
             }
-            const int rows_items = (H + RLE_ROWS_PER_ITEM - 1) / RLE_ROWS_PER_ITEM;
+            b.rows = item_rows(q);
+            const int rows_items = (H + b.rows - 1) / b.rows;
             int p = 0;
             auto add = [&](int kind, int items, int stage) {
                 b.phase_kind[p] = kind;

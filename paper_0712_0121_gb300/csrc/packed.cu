@@ -80,6 +80,7 @@ int packed_kmax(const PackedArgs &a) {
 
 size_t packed_smem_bytes(const PackedArgs &a) {
     if (!a.hmode) return 0;
+    if (a.nst == 1) return (size_t)PK_NBUF1 * a.rb * a.groups * a.slot_words * sizeof(uint32_t);
     return (size_t)a.nst * 2 * a.rb * a.groups * a.slot_words * sizeof(uint32_t);
 }
 

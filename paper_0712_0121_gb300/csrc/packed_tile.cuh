@@ -35,6 +35,7 @@
 #pragma once
 
 #include "counters.cuh"
+#include "cp_async.cuh"
 #include "morph_internal.cuh"
 
 namespace morph {
@@ -174,11 +175,10 @@ __host__ __device__ inline HPlan make_hplan(int sw, int ex) {
 }
 
 // HX1: both reaches <= 1 (rectangles up to 3 wide): one funnel shift per side.
+// Wn: the thread's words with HALO words on each side, in registers.
 template <int NWT, int HALO, bool HX1>
-__device__ __forceinline__ void h_stage(const uint32_t *win_smem, uint32_t (&out)[NWT], const HPlan &h) {
-    uint32_t Wn[NWT + 2 * HALO];
-#pragma unroll
-    for (int j = 0; j < NWT + 2 * HALO; ++j) Wn[j] = win_smem[j];
+__device__ __forceinline__ void h_stage_win(const uint32_t (&Wn)[NWT + 2 * HALO], uint32_t (&out)[NWT],
+                                            const HPlan &h) {
     if (HX1) {
 #pragma unroll
         for (int t = 0; t < NWT; ++t) {
@@ -194,10 +194,162 @@ __device__ __forceinline__ void h_stage(const uint32_t *win_smem, uint32_t (&out
     for (int t = 0; t < NWT; ++t) out[t] = r[t] & l[t];
 }
 
+template <int NWT, int HALO, bool HX1>
+__device__ __forceinline__ void h_stage(const uint32_t *win_smem, uint32_t (&out)[NWT], const HPlan &h) {
+    uint32_t Wn[NWT + 2 * HALO];
+#pragma unroll
+    for (int j = 0; j < NWT + 2 * HALO; ++j) Wn[j] = win_smem[j];
+    h_stage_win<NWT, HALO, HX1>(Wn, out, h);
+}
+
 // ------------------------------------------------------------- the tile
 // Rows per shared-memory exchange chunk: the chunk's global loads are issued
 // together, then consumed.
 constexpr int PK_RB = 8;
+
+// One-stage tile (erode / dilate with sw > 1).  Input rows are copied
+// asynchronously into a ring of shared-memory row slots, PK_NBUF1 chunks of
+// PK_RB rows deep (chunk c+2 is in flight while chunk c is processed); per
+// row each thread reads its words and HALO neighbour words from the slot,
+// runs the horizontal pass, then its column counters, and stores the word
+// pair.  One barrier per chunk; no register staging of future rows.
+constexpr int PK_NBUF1 = 3;
+
+template <int KMAX, int HALO, bool HX1>
+__device__ __forceinline__ void packed1_tile(const PackedArgs &a, int bx, int by, uint32_t *sm) {
+    constexpr int NWT = PK_NWT, RB = PK_RB, NBUF = PK_NBUF1;
+    constexpr int PAD = pk_pad(HALO), NWIN = NWT + 2 * HALO;
+    constexpr int KC = KMAX > 0 ? KMAX : 1;
+    static_assert(NWT == 2, "the tile moves word pairs");
+    const int tid = threadIdx.x;
+    const int tpr = a.tpr, groups = a.groups, band = a.band, H = a.H;
+    const int g = tid / tpr, lt = tid - g * tpr;
+    const bool act = g < groups;
+    const int gg = act ? g : 0;
+    const int strip0 = by * a.strip_words;
+    const int w0 = strip0 - a.halo_words + lt * NWT;
+    const int Y0 = (bx * groups + gg) * band;
+    const int wup = a.sh - 1;
+    const int iters = band + wup;
+    const int y_end = min(Y0 + band, H);
+    const int K = a.K;
+    uint32_t eqm[KC];
+#pragma unroll
+    for (int k = 0; k < KC; ++k) eqm[k] = a.eqm[k];
+    const HPlan hp = make_hplan(a.sw, a.ex[0]);
+    const uint32_t inm_in = a.inv_in ? ONES : 0u, inm_out = a.inv_out ? ONES : 0u;
+
+    // stage-input masks of the window words: padding bits and words outside
+    // the row become 1 whatever the slot holds there
+    uint32_t nmw[NWIN];
+#pragma unroll
+    for (int j = 0; j < NWIN; ++j) {
+        const int w = w0 - HALO + j;
+        nmw[j] = (w >= 0 && w < a.nw_valid) ? ~word_mask(w, a.W) : ONES;
+    }
+    uint32_t vmask[NWT];
+    bool st_ok[NWT], ld_ok[NWT];
+#pragma unroll
+    for (int t = 0; t < NWT; ++t) {
+        const int w = w0 + t;
+        ld_ok[t] = act && w >= 0 && w < a.nw_valid;
+        vmask[t] = ld_ok[t] ? word_mask(w, a.W) : 0u;
+        st_ok[t] = act && w >= strip0 && w < strip0 + a.strip_words && w < a.nw_cover;
+    }
+    const bool pair_ld = a.vec && ld_ok[0] && ld_ok[1];
+    const bool vec_st = a.vec && st_ok[0] && st_ok[1];
+    ColCounter<KC> cc[NWT];
+#pragma unroll
+    for (int t = 0; t < NWT; ++t) cc[t].reset();
+
+    const int r_first = Y0 - a.ey[0];
+    const int64_t sstride = a.sstride, dstride = a.dstride;
+    const uint32_t *src = a.src + w0;  // dereferenced only for words inside the row
+    uint32_t *dst = a.dst + w0;
+    const int row_words = groups * a.slot_words;       // between row slots of a chunk
+    const int buf_words = RB * row_words;              // between chunks
+    uint32_t *my = sm + gg * a.slot_words + PAD + lt * NWT;  // own pair, row 0, buffer 0
+
+    auto issue = [&](int c) {
+        if (act) {
+            uint32_t *b = my + (c % NBUF) * buf_words;
+            const int rb0 = r_first + c * RB;
+#pragma unroll
+            for (int i = 0; i < RB; ++i) {
+                const int r = rb0 + i;
+                uint32_t *d = b + i * row_words;
+                if (r >= 0 && r < H) {
+                    const uint32_t *p = src + (int64_t)r * sstride;
+                    if (pair_ld) {
+                        cp_async8(d, p);
+                    } else {
+                        if (ld_ok[0]) cp_async4(d, p);
+                        if (ld_ok[1]) cp_async4(d + 1, p + 1);
+                    }
+                } else {
+                    // outside the image: raw words whose stage input is all ones
+                    *reinterpret_cast<uint2 *>(d) = make_uint2(~inm_in, ~inm_in);
+                }
+            }
+        }
+        cp_async_commit();
+    };
+
+    const int nch = (iters + RB - 1) / RB;
+    issue(0);
+    if (nch > 1) issue(1);
+    for (int c = 0; c < nch; ++c) {
+        if (c + 1 < nch) cp_async_wait<1>();
+        else cp_async_wait<0>();
+        __syncthreads();
+        // buffer (c + 2) % NBUF was last read in chunk c - 1, before the barrier
+        if (c + 2 < nch) issue(c + 2);
+        const uint32_t *b = my + (c % NBUF) * buf_words;
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+            const int it = c * RB + i;
+            const uint32_t *wp = b + i * row_words - HALO;  // window start
+            uint32_t v[NWIN];
+            if constexpr (HALO % 2 == 0) {
+#pragma unroll
+                for (int j = 0; j < NWIN; j += 2) {
+                    const uint2 x = *reinterpret_cast<const uint2 *>(wp + j);
+                    v[j] = x.x;
+                    v[j + 1] = x.y;
+                }
+            } else {
+                v[0] = wp[0];
+#pragma unroll
+                for (int j = 1; j + 1 < NWIN; j += 2) {
+                    const uint2 x = *reinterpret_cast<const uint2 *>(wp + j);
+                    v[j] = x.x;
+                    v[j + 1] = x.y;
+                }
+                v[NWIN - 1] = wp[NWIN - 1];
+            }
+#pragma unroll
+            for (int j = 0; j < NWIN; ++j) v[j] = (v[j] ^ inm_in) | nmw[j];
+            uint32_t h[NWT];
+            h_stage_win<NWT, HALO, HX1>(v, h, hp);
+            if (KMAX > 0) {
+#pragma unroll
+                for (int t = 0; t < NWT; ++t) h[t] = cc[t].push(h[t], K, eqm);
+            }
+            const int y = Y0 + it - wup;
+            if (it >= wup && y < y_end) {
+                const uint32_t o0 = (h[0] ^ inm_out) & vmask[0];
+                const uint32_t o1 = (h[1] ^ inm_out) & vmask[1];
+                uint32_t *p = dst + (int64_t)y * dstride;
+                if (vec_st) {
+                    *reinterpret_cast<uint2 *>(p) = make_uint2(o0, o1);
+                } else {
+                    if (st_ok[0]) p[0] = o0;
+                    if (st_ok[1]) p[1] = o1;
+                }
+            }
+        }
+    }
+}
 
 // Template parameters: NST stages (1 or 2), HS (horizontal stage present,
 // i.e. sw > 1), KMAX (bit planes of the column counters, >= K; 0 when sh ==
@@ -205,7 +357,7 @@ constexpr int PK_RB = 8;
 // reach), HX1 (horizontal reach <= 1 on both sides).  bx: row-band block index, by:
 // column-strip index.  sm: dynamic shared memory of packed_smem_bytes().
 template <int NST, bool HS, int KMAX, int HALO, bool HX1>
-__device__ __forceinline__ void packed_tile(const PackedArgs &a, int bx, int by, uint32_t *sm) {
+__device__ __forceinline__ void packed_tile2(const PackedArgs &a, int bx, int by, uint32_t *sm) {
     constexpr int NWT = PK_NWT;
     constexpr int RB = PK_RB;
     constexpr int PAD = pk_pad(HALO);
@@ -421,6 +573,15 @@ __device__ __forceinline__ void packed_tile(const PackedArgs &a, int bx, int by,
                 if (it >= wup && y < y_end) store_row(y, h);
             }
         }
+    }
+}
+
+template <int NST, bool HS, int KMAX, int HALO, bool HX1>
+__device__ __forceinline__ void packed_tile(const PackedArgs &a, int bx, int by, uint32_t *sm) {
+    if constexpr (NST == 1 && HS) {
+        packed1_tile<KMAX, HALO, HX1>(a, bx, by, sm);
+    } else {
+        packed_tile2<NST, HS, KMAX, HALO, HX1>(a, bx, by, sm);
     }
 }
 

@@ -12,6 +12,7 @@
 #pragma once
 
 #include "counters.cuh"
+#include "cp_async.cuh"
 #include "morph_internal.cuh"
 
 namespace morph {
@@ -22,19 +23,6 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
-}
-
-// Asynchronous 4-byte global -> shared copy (no register round trip); the
-// copies a thread issued complete at cp_async_wait<n> (all but its n most
-// recent groups), and become visible to the CTA after a barrier.
-__device__ __forceinline__ void cp_async4(uint32_t *sdst, const uint32_t *gsrc) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 __device__ __forceinline__ int warp_excl_scan(int v, int lane, int &total) {

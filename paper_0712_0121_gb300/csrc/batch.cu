@@ -365,14 +365,18 @@ int bitlen(int v) {
     return k;
 }
 
+// Column-counter class of the batch's packed variants for sh: index into
+// {0, 2, 6, 16} planes.
+int batch_kidx(int km) {
+    if (km == 0) return 0;
+    if (km == 2) return 1;  // sh == 3 window
+    if (km <= 6) return 2;
+    return 3;
+}
+constexpr int BATCH_KMAX[4] = {0, 2, 6, 16};
+
 int packed_variant(const PackedArgs &a) {
-    const int kidx = [&] {
-        const int km = packed_kmax(a);
-        if (km == 0) return 0;
-        if (km == 2) return 1;  // sh == 3 window
-        if (km <= 6) return 2;
-        return 3;
-    }();
+    const int kidx = batch_kidx(packed_kmax(a));
     int h;
     if (!a.hmode) h = 0;
     else if (a.sw <= 3 && a.ex[0] <= 1 && a.sw - 1 - a.ex[0] <= 1) h = 1;
@@ -490,8 +494,17 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
             a.H = H;
             a.nw_valid = (W + 31) / 32;
             a.nw_cover = nw_cover;
+            const int kmax_class = [&] {
+                // packed_kmax() of this rectangle, mapped to the batch's classes
+                PackedArgs t{};
+                t.sh = c.sh;
+                int k = 0;
+                for (int v = c.sh; v; v >>= 1) ++k;
+                t.K = k;
+                return BATCH_KMAX[batch_kidx(packed_kmax(t))];
+            }();
             if (packed_plan(a, q.op, c.sw, c.sh, c.ox, c.oy, q.tile_rows ? q.tile_rows : tile_rows,
-                            MAX_THREADS) != 0)
+                            MAX_THREADS, kmax_class) != 0)
                 return berr(MORPH_EINVAL, "rectangle reaches more than 128 pixels sideways", j);
             b.variant = packed_variant(a);
             const dim3 g = packed_grid(a);

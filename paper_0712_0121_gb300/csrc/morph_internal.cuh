@@ -73,12 +73,15 @@ struct PackedArgs {
     int halo_words;       // extra computed words on each side of a strip
     int nstrips;
     int slot_words;       // smem words per group row slot
-    int vec;              // 64-bit loads / stores allowed (aligned bases, even strides)
+    int nwt;              // u32 words per thread
+    int vec;              // vector loads / stores of a thread's words allowed (aligned bases and strides)
 };
 
 int packed_halo(int sw, int ex);   // register-window halo words of the H stage (0: too wide)
+// kmax_class: the column-counter planes of the kernel set that will run the
+// plan (the batch kernel instantiates fewer classes); -1 = packed_kmax().
 int packed_plan(PackedArgs &a, int op, int sw, int sh, int ox, int oy, int band_rows_hint,
-                int block_threads_hint);
+                int block_threads_hint, int kmax_class = -1);
 size_t packed_smem_bytes(const PackedArgs &a);
 int packed_kmax(const PackedArgs &a);
 int packed_threads(const PackedArgs &a);

@@ -80,7 +80,7 @@ int packed_kmax(const PackedArgs &a) {
 
 size_t packed_smem_bytes(const PackedArgs &a) {
     if (!a.hmode) return 0;
-    if (a.nst == 1) return (size_t)PK_NBUF1 * a.rb * a.groups * a.slot_words * sizeof(uint32_t);
+    if (a.nst == 1) return (size_t)PK_NBUF1 * pk1_rb(a.nwt) * a.groups * a.slot_words * sizeof(uint32_t);
     return (size_t)a.nst * 2 * a.rb * a.groups * a.slot_words * sizeof(uint32_t);
 }
 
@@ -93,7 +93,7 @@ dim3 packed_grid(const PackedArgs &a) {
 // Fill the stage and tiling parameters.  Returns 0 on success, -1 if the
 // rectangle is too wide for the horizontal register window.
 int packed_plan(PackedArgs &a, int op, int sw, int sh, int ox, int oy, int band_hint,
-                int threads_hint) {
+                int threads_hint, int kmax_class) {
     const int rx = sw - 1 - ox, ry = sh - 1 - oy;
     a.sw = sw;
     a.sh = sh;
@@ -118,7 +118,13 @@ int packed_plan(PackedArgs &a, int op, int sw, int sh, int ox, int oy, int band_
     int max_threads = threads_hint > 0 ? threads_hint : MAX_THREADS;
     if (max_threads > MAX_THREADS) max_threads = MAX_THREADS;
     if (max_threads < 32) max_threads = 32;
-    const int cover_threads = (a.nw_cover + PK_NWT - 1) / PK_NWT;
+    // words per thread: the one-stage tile picks 2 or 4 (see pk1_nwt), the
+    // two-stage tile moves 2
+    const bool one_stage = a.nst == 1 && a.hmode;
+    const bool hx1 = sw <= 3 && a.ex[0] <= 1 && sw - 1 - a.ex[0] <= 1;
+    const int nwt = one_stage ? pk1_nwt(hx1, kmax_class >= 0 ? kmax_class : packed_kmax(a)) : PK_NWT;
+    a.nwt = nwt;
+    const int cover_threads = (a.nw_cover + nwt - 1) / nwt;
     if (cover_threads <= max_threads) {
         a.tpr = cover_threads;
         a.groups = max_threads / cover_threads;
@@ -128,8 +134,8 @@ int packed_plan(PackedArgs &a, int op, int sw, int sh, int ox, int oy, int band_
     } else {
         a.tpr = max_threads;
         a.groups = 1;
-        a.halo_words = ((a.nst * halo + PK_NWT - 1) / PK_NWT) * PK_NWT;
-        a.strip_words = max_threads * PK_NWT - 2 * a.halo_words;
+        a.halo_words = ((a.nst * halo + nwt - 1) / nwt) * nwt;
+        a.strip_words = max_threads * nwt - 2 * a.halo_words;
         a.nstrips = (a.nw_cover + a.strip_words - 1) / a.strip_words;
     }
     a.rb = PK_RB;
@@ -144,9 +150,11 @@ int packed_plan(PackedArgs &a, int op, int sw, int sh, int ox, int oy, int band_
         a.groups = (hcap + a.band - 1) / a.band;
         if (a.groups < 1) a.groups = 1;
     }
-    a.slot_words = a.tpr * PK_NWT + 2 * pk_pad(halo);
-    a.vec = ((uintptr_t)a.src % 8 == 0) && ((uintptr_t)a.dst % 8 == 0) && (a.sstride % 2 == 0) &&
-            (a.dstride % 2 == 0);
+    a.slot_words = a.tpr * nwt + 2 * (one_stage ? pk1_pad(halo, nwt) : pk_pad(halo));
+    // vector loads / stores of a thread's words: 16 bytes (one stage) or 8
+    const int vb = nwt * 4;
+    a.vec = ((uintptr_t)a.src % vb == 0) && ((uintptr_t)a.dst % vb == 0) && (a.sstride % nwt == 0) &&
+            (a.dstride % nwt == 0);
     return 0;
 }
 

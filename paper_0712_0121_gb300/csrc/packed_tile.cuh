@@ -208,19 +208,83 @@ __device__ __forceinline__ void h_stage(const uint32_t *win_smem, uint32_t (&out
 constexpr int PK_RB = 8;
 
 // One-stage tile (erode / dilate with sw > 1).  Input rows are copied
-// asynchronously into a ring of shared-memory row slots, PK_NBUF1 chunks of
-// PK_RB rows deep (chunk c+2 is in flight while chunk c is processed); per
-// row each thread reads its words and HALO neighbour words from the slot,
-// runs the horizontal pass, then its column counters, and stores the word
-// pair.  One barrier per chunk; no register staging of future rows.
+// asynchronously into a ring of shared-memory row slots, PK_NBUF1 chunks
+// deep (chunk c+2 is in flight while chunk c is processed); per row each
+// thread reads its NWT words and HALO neighbour words from the slot, runs
+// the horizontal pass, then its column counters, and stores its words.  One
+// barrier per chunk; no register staging of future rows.  NWT = 4 amortises
+// the per-row address and predicate work and the halo words of the
+// horizontal doubling over more words; NWT = 2 keeps fewer registers where
+// the work per word is small (reach 1) or the counters are deep (sh >= 32).
 constexpr int PK_NBUF1 = 3;
 
-template <int KMAX, int HALO, bool HX1>
+__host__ __device__ constexpr int pk1_nwt(bool hx1, int kmax) { return (hx1 || kmax >= 6) ? 2 : 4; }
+__host__ __device__ constexpr int pk1_rb(int nwt) { return nwt == 4 ? 4 : 8; }
+// slot pad: a multiple of NWT words, so that each thread's words start on
+// an NWT*4-byte boundary of the slot
+__host__ __device__ constexpr int pk1_pad(int halo, int nwt) { return (halo + nwt - 1) / nwt * nwt; }
+
+template <int NWT>
+struct WordsT;
+template <>
+struct WordsT<2> {
+    using V = uint2;
+    __device__ static void cp(uint32_t *d, const uint32_t *p) { cp_async8(d, p); }
+    __device__ static V make(uint32_t x) { return make_uint2(x, x); }
+};
+template <>
+struct WordsT<4> {
+    using V = uint4;
+    __device__ static void cp(uint32_t *d, const uint32_t *p) { cp_async16(d, p); }
+    __device__ static V make(uint32_t x) { return make_uint4(x, x, x, x); }
+};
+
+// The thread's window (HALO words, its NWT words at `own`, HALO words) from
+// shared memory with the widest aligned vector loads (own is NWT-word
+// aligned).
+template <int NWT, int HALO>
+__device__ __forceinline__ void lds_window(const uint32_t *own, uint32_t (&v)[NWT + 2 * HALO]) {
+    constexpr int NWIN = NWT + 2 * HALO;
+    auto ld2 = [&](int j, int o) {
+        const uint2 x = *reinterpret_cast<const uint2 *>(own + o);
+        v[j] = x.x;
+        v[j + 1] = x.y;
+    };
+    auto ld4 = [&](int j, int o) {
+        const uint4 x = *reinterpret_cast<const uint4 *>(own + o);
+        v[j] = x.x;
+        v[j + 1] = x.y;
+        v[j + 2] = x.z;
+        v[j + 3] = x.w;
+    };
+    if constexpr (HALO % NWT == 0) {
+#pragma unroll
+        for (int j = 0; j < NWIN; j += NWT) {
+            if constexpr (NWT == 4) ld4(j, j - HALO);
+            else ld2(j, j - HALO);
+        }
+    } else if constexpr (HALO == 1) {
+        v[0] = own[-1];
+        if constexpr (NWT == 4) ld4(1, 0);
+        else ld2(1, 0);
+        v[NWIN - 1] = own[NWT];
+    } else {
+        static_assert(NWT == 4 && HALO == 2, "window layout");
+        ld2(0, -2);
+        ld4(2, 0);
+        ld2(6, 4);
+    }
+}
+
+template <int NWT, int KMAX, int HALO, bool HX1>
 __device__ __forceinline__ void packed1_tile(const PackedArgs &a, int bx, int by, uint32_t *sm) {
-    constexpr int NWT = PK_NWT, RB = PK_RB, NBUF = PK_NBUF1;
-    constexpr int PAD = pk_pad(HALO), NWIN = NWT + 2 * HALO;
+    constexpr int RB = pk1_rb(NWT), NBUF = PK_NBUF1;
+    constexpr int PAD = pk1_pad(HALO, NWT), NWIN = NWT + 2 * HALO;
     constexpr int KC = KMAX > 0 ? KMAX : 1;
-    static_assert(NWT == 2, "the tile moves word pairs");
+    using WT = WordsT<NWT>;
+    // the plan's layout (threads per row, slot size, shared memory) is made
+    // for a.nwt words per thread; never run this body on another layout
+    if (a.nwt != NWT) return;
     const int tid = threadIdx.x;
     const int tpr = a.tpr, groups = a.groups, band = a.band, H = a.H;
     const int g = tid / tpr, lt = tid - g * tpr;
@@ -249,15 +313,19 @@ __device__ __forceinline__ void packed1_tile(const PackedArgs &a, int bx, int by
     }
     uint32_t vmask[NWT];
     bool st_ok[NWT], ld_ok[NWT];
+    bool all_ld = true, all_st = true;
 #pragma unroll
     for (int t = 0; t < NWT; ++t) {
         const int w = w0 + t;
         ld_ok[t] = act && w >= 0 && w < a.nw_valid;
         vmask[t] = ld_ok[t] ? word_mask(w, a.W) : 0u;
         st_ok[t] = act && w >= strip0 && w < strip0 + a.strip_words && w < a.nw_cover;
+        all_ld = all_ld && ld_ok[t];
+        all_st = all_st && st_ok[t];
     }
-    const bool pair_ld = a.vec && ld_ok[0] && ld_ok[1];
-    const bool vec_st = a.vec && st_ok[0] && st_ok[1];
+    // a.vec: bases aligned to NWT words and strides multiples of NWT words
+    const bool vec_ld = a.vec && all_ld;
+    const bool vec_st = a.vec && all_st;
     ColCounter<KC> cc[NWT];
 #pragma unroll
     for (int t = 0; t < NWT; ++t) cc[t].reset();
@@ -268,7 +336,7 @@ __device__ __forceinline__ void packed1_tile(const PackedArgs &a, int bx, int by
     uint32_t *dst = a.dst + w0;
     const int row_words = groups * a.slot_words;       // between row slots of a chunk
     const int buf_words = RB * row_words;              // between chunks
-    uint32_t *my = sm + gg * a.slot_words + PAD + lt * NWT;  // own pair, row 0, buffer 0
+    uint32_t *my = sm + gg * a.slot_words + PAD + lt * NWT;  // own words, row 0, buffer 0
 
     auto issue = [&](int c) {
         if (act) {
@@ -280,15 +348,16 @@ __device__ __forceinline__ void packed1_tile(const PackedArgs &a, int bx, int by
                 uint32_t *d = b + i * row_words;
                 if (r >= 0 && r < H) {
                     const uint32_t *p = src + (int64_t)r * sstride;
-                    if (pair_ld) {
-                        cp_async8(d, p);
+                    if (vec_ld) {
+                        WT::cp(d, p);
                     } else {
-                        if (ld_ok[0]) cp_async4(d, p);
-                        if (ld_ok[1]) cp_async4(d + 1, p + 1);
+#pragma unroll
+                        for (int t = 0; t < NWT; ++t)
+                            if (ld_ok[t]) cp_async4(d + t, p + t);
                     }
                 } else {
                     // outside the image: raw words whose stage input is all ones
-                    *reinterpret_cast<uint2 *>(d) = make_uint2(~inm_in, ~inm_in);
+                    *reinterpret_cast<typename WT::V *>(d) = WT::make(~inm_in);
                 }
             }
         }
@@ -308,25 +377,8 @@ __device__ __forceinline__ void packed1_tile(const PackedArgs &a, int bx, int by
 #pragma unroll
         for (int i = 0; i < RB; ++i) {
             const int it = c * RB + i;
-            const uint32_t *wp = b + i * row_words - HALO;  // window start
             uint32_t v[NWIN];
-            if constexpr (HALO % 2 == 0) {
-#pragma unroll
-                for (int j = 0; j < NWIN; j += 2) {
-                    const uint2 x = *reinterpret_cast<const uint2 *>(wp + j);
-                    v[j] = x.x;
-                    v[j + 1] = x.y;
-                }
-            } else {
-                v[0] = wp[0];
-#pragma unroll
-                for (int j = 1; j + 1 < NWIN; j += 2) {
-                    const uint2 x = *reinterpret_cast<const uint2 *>(wp + j);
-                    v[j] = x.x;
-                    v[j + 1] = x.y;
-                }
-                v[NWIN - 1] = wp[NWIN - 1];
-            }
+            lds_window<NWT, HALO>(b + i * row_words, v);
 #pragma unroll
             for (int j = 0; j < NWIN; ++j) v[j] = (v[j] ^ inm_in) | nmw[j];
             uint32_t h[NWT];
@@ -337,14 +389,23 @@ __device__ __forceinline__ void packed1_tile(const PackedArgs &a, int bx, int by
             }
             const int y = Y0 + it - wup;
             if (it >= wup && y < y_end) {
-                const uint32_t o0 = (h[0] ^ inm_out) & vmask[0];
-                const uint32_t o1 = (h[1] ^ inm_out) & vmask[1];
+                uint32_t o[NWT];
+#pragma unroll
+                for (int t = 0; t < NWT; ++t) o[t] = (h[t] ^ inm_out) & vmask[t];
                 uint32_t *p = dst + (int64_t)y * dstride;
                 if (vec_st) {
-                    *reinterpret_cast<uint2 *>(p) = make_uint2(o0, o1);
+                    typename WT::V x;
+                    x.x = o[0];
+                    x.y = o[1];
+                    if constexpr (NWT == 4) {
+                        x.z = o[2];
+                        x.w = o[3];
+                    }
+                    *reinterpret_cast<typename WT::V *>(p) = x;
                 } else {
-                    if (st_ok[0]) p[0] = o0;
-                    if (st_ok[1]) p[1] = o1;
+#pragma unroll
+                    for (int t = 0; t < NWT; ++t)
+                        if (st_ok[t]) p[t] = o[t];
                 }
             }
         }
@@ -579,7 +640,7 @@ __device__ __forceinline__ void packed_tile2(const PackedArgs &a, int bx, int by
 template <int NST, bool HS, int KMAX, int HALO, bool HX1>
 __device__ __forceinline__ void packed_tile(const PackedArgs &a, int bx, int by, uint32_t *sm) {
     if constexpr (NST == 1 && HS) {
-        packed1_tile<KMAX, HALO, HX1>(a, bx, by, sm);
+        packed1_tile<pk1_nwt(HX1, KMAX), KMAX, HALO, HX1>(a, bx, by, sm);
     } else {
         packed_tile2<NST, HS, KMAX, HALO, HX1>(a, bx, by, sm);
     }

@@ -60,6 +60,10 @@ def _load():
                 f = getattr(lib, name)
                 f.argtypes = [u8p, u8p, ci, ci, ci, ci, ci, ci, ci]
                 f.restype = ci
+            for name in ("oracle_erode_mask", "oracle_dilate_mask"):
+                f = getattr(lib, name)
+                f.argtypes = [u8p, u8p, ci, ci, u8p, ci, ci, ci, ci, ci]
+                f.restype = None
             lib.oracle_rect_batch.argtypes = [u8p, u8p, ctypes.c_int64, ci, ci, ci, ci, ci, ci, ci]
             lib.oracle_rect_batch.restype = ci
             lib.oracle_rle_count.argtypes = [i32p, u8p, ci, ci]
@@ -161,6 +165,123 @@ def rect_batch(imgs: np.ndarray, sw, sh, ox, oy, op: str) -> np.ndarray:
                                  sw, sh, ox, oy, code):
         raise MemoryError("oracle batch: allocation failed")
     return out
+
+
+# ----------------------------------------------------------------- masks
+# Section "Morphology with Arbitrary Masks": the structuring element is a
+# bitmap ``uint8[mh, mw]`` (1 = in the element) with origin (ox, oy); the
+# definitions are the rectangle ones over the element's pixels (see
+# ``oracle_erode_mask`` in morph_oracle.c).  Two evaluation modes:
+#   brute — the pixel-at-a-time definition (C);
+#   runs  — the paper's run-at-a-time loop: for every horizontal run of the
+#           element, the image's clipped row minimum over the run's pixels,
+#           shifted to the run's place, ANDed into the result (numpy; the
+#           image is embedded in an all-ones canvas so that the clipped
+#           window is a plain window).
+
+def _as_mask(mask) -> np.ndarray:
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    if m.ndim != 2 or m.size == 0:
+        raise ValueError("mask must be a non-empty 2D array")
+    m = (m != 0).astype(np.uint8)
+    if not m.any():
+        raise ValueError("mask has no pixel")
+    return m
+
+
+def mask_runs(mask):
+    """Horizontal runs of the element: list of (j, x0, w), row by row, left
+    to right (the runs the paper's loop iterates over)."""
+    m = _as_mask(mask)
+    out = []
+    for j in range(m.shape[0]):
+        d = np.diff(np.concatenate(([0], m[j].astype(np.int8), [0])))
+        starts, ends = np.flatnonzero(d == 1), np.flatnonzero(d == -1)
+        out += [(j, int(a), int(b - a)) for a, b in zip(starts, ends)]
+    return out
+
+
+def reflect_mask(mask, ox, oy):
+    """The reflected element (i, j) -> (mw-1-i, mh-1-j) and its origin."""
+    m = _as_mask(mask)
+    return m[::-1, ::-1].copy(), m.shape[1] - 1 - ox, m.shape[0] - 1 - oy
+
+
+def _mask_call(img, mask, ox, oy, threads, dilate):
+    m = _as_mask(mask)
+    mh, mw = m.shape
+    if not (0 <= ox < mw and 0 <= oy < mh):
+        raise ValueError("origin outside the mask")
+    a = _as_img(img)
+    H, W = a.shape
+    out = np.empty_like(a)
+    if a.size:
+        f = _load().oracle_dilate_mask if dilate else _load().oracle_erode_mask
+        f(_ptr(out, ctypes.c_uint8), _ptr(a, ctypes.c_uint8), W, H, _ptr(m, ctypes.c_uint8), mw, mh,
+          ox, oy, threads)
+    return out
+
+
+def _erode_mask_runs(img, mask, ox, oy):
+    m = _as_mask(mask)
+    mh, mw = m.shape
+    a = _as_img(img)
+    H, W = a.shape
+    P = max(mw, mh)
+    canvas = np.ones((H + 2 * P, W + 2 * P), np.uint8)
+    canvas[P:P + H, P:P + W] = a
+    Wc = canvas.shape[1]
+    out = np.ones((H, W), np.uint8)
+    for j, x0, w in mask_runs(m):
+        # S[:, x] = min of canvas[:, x .. x+w-1]: the run's pixels, left end at x
+        S = canvas[:, 0:Wc - w + 1].copy()
+        for i in range(1, w):
+            np.minimum(S, canvas[:, i:Wc - w + 1 + i], out=S)
+        dy, dx = j - oy, x0 - ox
+        out &= S[P + dy:P + dy + H, P + dx:P + dx + W]
+    return out
+
+
+def erode_mask(img, mask, ox, oy, mode="brute", threads=1) -> np.ndarray:
+    """Clipped-window erosion by an arbitrary element with origin (ox, oy)."""
+    if mode == "brute":
+        return _mask_call(img, mask, ox, oy, threads, dilate=False)
+    if mode == "runs":
+        m = _as_mask(mask)
+        if not (0 <= ox < m.shape[1] and 0 <= oy < m.shape[0]):
+            raise ValueError("origin outside the mask")
+        return _erode_mask_runs(img, m, ox, oy)
+    raise ValueError("mode must be 'brute' or 'runs'")
+
+
+def dilate_mask(img, mask, ox, oy, mode="brute", threads=1) -> np.ndarray:
+    """Clipped-window dilation by an arbitrary element (reflected window)."""
+    if mode == "brute":
+        return _mask_call(img, mask, ox, oy, threads, dilate=True)
+    if mode == "runs":
+        # the max over the reflected window is 1 - the min of the complement
+        r, rx, ry = reflect_mask(mask, ox, oy)
+        return 1 - _erode_mask_runs(1 - _as_img(img), r, rx, ry)
+    raise ValueError("mode must be 'brute' or 'runs'")
+
+
+def apply_mask(op: str, img, mask, ox, oy, mode="brute", threads=1) -> np.ndarray:
+    """erode / dilate / open (= dilate of erode) / close (= erode of dilate)."""
+    if op == "erode":
+        return erode_mask(img, mask, ox, oy, mode, threads)
+    if op == "dilate":
+        return dilate_mask(img, mask, ox, oy, mode, threads)
+    if op == "open":
+        return dilate_mask(erode_mask(img, mask, ox, oy, mode, threads), mask, ox, oy, mode, threads)
+    if op == "close":
+        return erode_mask(dilate_mask(img, mask, ox, oy, mode, threads), mask, ox, oy, mode, threads)
+    raise ValueError("op must be erode, dilate, open or close")
+
+
+def disc_mask(r: int) -> np.ndarray:
+    """Digital disc of radius r: (i-r)^2 + (j-r)^2 <= r^2, size (2r+1)^2."""
+    j, i = np.mgrid[0:2 * r + 1, 0:2 * r + 1]
+    return (((i - r) ** 2 + (j - r) ** 2) <= r * r).astype(np.uint8)
 
 
 # ----------------------------------------------------------------- RLE

@@ -107,6 +107,61 @@ EXPORT void oracle_dilate_rect(uint8_t *out, const uint8_t *in, int W, int H,
     }
 }
 
+/* ---------------------------------------------------------------- masks */
+
+/* Section "Morphology with Arbitrary Masks": the structuring element is a
+ * bitmap, mask[j * mw + i] != 0 when (i, j) belongs to it, origin (ox, oy).
+ * The definitions are the rectangle ones with the window replaced by the
+ * element's pixels (same clipped-window reading):
+ *   E(x,y) = min { I(x+i-ox, y+j-oy) : mask(i,j), inside image }
+ *   D(x,y) = max { I(x-i+ox, y-j+oy) : mask(i,j), inside image }
+ * This is the paper's pixel-at-a-time loop, kept as the reference. */
+EXPORT void oracle_erode_mask(uint8_t *out, const uint8_t *in, int W, int H,
+                              const uint8_t *mask, int mw, int mh, int ox, int oy,
+                              int nthreads) {
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 8) if (nthreads > 1)
+    for (int y = 0; y < H; y++) {
+        for (int x = 0; x < W; x++) {
+            uint8_t v = 1;
+            for (int j = 0; j < mh && v; j++) {
+                int yy = y + j - oy;
+                if (yy < 0 || yy >= H) continue;
+                for (int i = 0; i < mw; i++) {
+                    if (!mask[j * mw + i]) continue;
+                    int xx = x + i - ox;
+                    if (xx < 0 || xx >= W) continue;
+                    if (in[(size_t)yy * W + xx] == 0) { v = 0; break; }
+                }
+            }
+            out[(size_t)y * W + x] = v;
+        }
+    }
+}
+
+EXPORT void oracle_dilate_mask(uint8_t *out, const uint8_t *in, int W, int H,
+                               const uint8_t *mask, int mw, int mh, int ox, int oy,
+                               int nthreads) {
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 8) if (nthreads > 1)
+    for (int y = 0; y < H; y++) {
+        for (int x = 0; x < W; x++) {
+            uint8_t v = 0;
+            for (int j = 0; j < mh && !v; j++) {
+                int yy = y - j + oy;
+                if (yy < 0 || yy >= H) continue;
+                for (int i = 0; i < mw; i++) {
+                    if (!mask[j * mw + i]) continue;
+                    int xx = x - i + ox;
+                    if (xx < 0 || xx >= W) continue;
+                    if (in[(size_t)yy * W + xx] != 0) { v = 1; break; }
+                }
+            }
+            out[(size_t)y * W + x] = v;
+        }
+    }
+}
+
 /* ----------------------------------------------------------- separable */
 
 /* 1D pass along rows: window of sw pixels, origin ox; erode = min, dilate =

@@ -352,12 +352,28 @@ def run_probe(args):
         pass
     results = []
     for se in args.probe_se.split(","):
-        sw, sh = (int(v) for v in se.split("x"))
-        if args.probe == "packed":
+        if args.probe == "mask":
+            # "d<r>": digital disc of radius r; "WxH": the full rectangle as a mask
+            if se.startswith("d"):
+                r = int(se[1:])
+                jj, ii = np.mgrid[0:2 * r + 1, 0:2 * r + 1]
+                mask = (((ii - r) ** 2 + (jj - r) ** 2) <= r * r).astype(np.uint8)
+            else:
+                mw, mh = (int(v) for v in se.split("x"))
+                mask = np.ones((mh, mw), np.uint8)
+            dst = M.Packed.empty(Wt, Ht, 64)
+            ox, oy = mask.shape[1] // 2, mask.shape[0] // 2
+            ws = torch.empty(max(1, M.mask_workspace_size(args.probe_op, dst, src, mask, ox, oy)),
+                             dtype=torch.uint8, device="cuda")
+            fn = lambda: M.morph_mask(args.probe_op, dst, src, mask, ox, oy, workspace=ws)  # noqa: E731
+            alg = 2 * page_bytes
+        elif args.probe == "packed":
+            sw, sh = (int(v) for v in se.split("x"))
             dst = M.Packed.empty(Wt, Ht, 64)
             fn = lambda: M.morph_rect(args.probe_op, dst, src, sw, sh)  # noqa: E731
             alg = 2 * page_bytes
         else:
+            sw, sh = (int(v) for v in se.split("x"))
             cap = Ht * args.rle_runs_per_row
             a, b = M.Rle.empty(Wt, Ht, cap), M.Rle.empty(Wt, Ht, cap)
             out = M.Packed.empty(Wt, Ht, 64)
@@ -584,7 +600,7 @@ def main():
     ap.add_argument("--batch-pages", type=int, default=256)
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--tune-cache", default=os.path.join("/tmp", "morph_tune_cache.json"))
-    ap.add_argument("--probe", choices=["packed", "rle"], default=None,
+    ap.add_argument("--probe", choices=["packed", "rle", "mask"], default=None,
                     help="run one standalone op on a tall page stack (ncu target) and exit")
     ap.add_argument("--probe-op", default="erode")
     ap.add_argument("--probe-se", default="3x3")

@@ -173,6 +173,34 @@ MORPH_API morph_status morph_rle_rect_noalloc(int op, const morph_image *dst,
                                               const morph_image *src, int se_w, int se_h,
                                               int origin_x, int origin_y, void *stream);
 
+/* ------------------------------------------------------- arbitrary masks --
+ * Section "Morphology with Arbitrary Masks": erosion / dilation / opening /
+ * closing of a packed image by an arbitrary structuring element.
+ *   mask: HOST memory, mask_h rows of mask_w bytes, row 0 first; a nonzero
+ *         byte puts that pixel (i, j) in the element (read during the call
+ *         only).  1 <= mask_w, mask_h <= 4096; at least one pixel; at most
+ *         1024 horizontal runs (maximal row segments of set pixels).
+ *   origin (origin_x, origin_y) inside the mask (it need not be set).
+ * Semantics are the rectangle ones with the window replaced by the element:
+ *   E(x,y) = AND of src(x+i-ox, y+j-oy) over set (i,j) inside the image,
+ *   D(x,y) = OR of src(x-i+ox, y-j+oy) over set (i,j) inside the image,
+ *   open = D(E), close = E(D); a full mask gives exactly morph_rect.
+ * Run at a time with doubling accumulation: doubling levels of the image up
+ * to the longest run are built in the workspace, then every output word is
+ * the AND of two level words per run.  src and dst packed (either word size),
+ * same size, not overlapping.  Workspace (device, 256-byte aligned):
+ * morph_mask_workspace_size() bytes (0 = none needed; that function returns
+ * 0 also for invalid arguments, which morph_mask then reports).  Errors:
+ * MORPH_EINVAL (arguments, RLE images, empty or too large element),
+ * MORPH_ENOMEM (workspace too small), MORPH_ECUDA. */
+MORPH_API size_t morph_mask_workspace_size(int op, const morph_image *dst, const morph_image *src,
+                                           const uint8_t *mask, int mask_w, int mask_h,
+                                           int origin_x, int origin_y);
+MORPH_API morph_status morph_mask(int op, const morph_image *dst, const morph_image *src,
+                                  const uint8_t *mask, int mask_w, int mask_h, int origin_x,
+                                  int origin_y, void *workspace, size_t workspace_bytes,
+                                  void *stream);
+
 /* ------------------------------------------------------------ conversion --
  * Section "Conversion Between Image Formats".
  * rle_from_bitmap: packed src -> RLE dst (canonical runs of every row).  A

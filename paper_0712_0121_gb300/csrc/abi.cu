@@ -284,6 +284,66 @@ morph_status run_rle(int op, const morph_image *dst, const morph_image *src, Se 
     return MORPH_OK;
 }
 
+// ------------------------------------------------------ arbitrary masks
+// Runs of the element (reflected for a dilation stage) into a.runs; fills
+// a.nruns and a.nlev.  Errors: no pixel, too many runs.
+morph_status mask_runs(const uint8_t *mask, int mw, int mh, int ox, int oy, bool reflect,
+                       MaskArgs &a) {
+    int n = 0, nlev = 0;
+    const int rox = reflect ? mw - 1 - ox : ox, roy = reflect ? mh - 1 - oy : oy;
+    for (int j = 0; j < mh; ++j) {
+        const uint8_t *row = mask + (size_t)(reflect ? mh - 1 - j : j) * mw;
+        auto in = [&](int i) { return row[reflect ? mw - 1 - i : i] != 0; };
+        for (int i = 0; i < mw;) {
+            if (!in(i)) { ++i; continue; }
+            const int x0 = i;
+            while (i < mw && in(i)) ++i;
+            const int w = i - x0;
+            if (n == MASK_MAX_RUNS)
+                return fail(MORPH_EINVAL, "structuring element has more than %d horizontal runs",
+                            MASK_MAX_RUNS);
+            int m = 0;
+            while ((2 << m) <= w) ++m;
+            MaskRun &u = a.runs[n++];
+            u.dy = (int16_t)(j - roy);
+            u.dx1 = (int16_t)(x0 - rox);
+            u.dx2 = (int16_t)(x0 - rox + w - (1 << m));
+            u.m = (int16_t)m;
+            if (m > nlev) nlev = m;
+        }
+    }
+    if (n == 0) return fail(MORPH_EINVAL, "structuring element has no pixel");
+    a.nruns = n;
+    a.nlev = nlev;
+    return MORPH_OK;
+}
+
+morph_status check_mask_args(int op, const morph_image *dst, const morph_image *src,
+                             const uint8_t *mask, int mw, int mh, int ox, int oy) {
+    morph_status st = check_image(src, "src");
+    if (st) return st;
+    if ((st = check_image(dst, "dst"))) return st;
+    if (op < MORPH_ERODE || op > MORPH_CLOSE) return fail(MORPH_EINVAL, "op %d is not a morph_op", op);
+    if (!is_packed(src->fmt) || !is_packed(dst->fmt))
+        return fail(MORPH_EINVAL, "arbitrary masks take packed images");
+    if (dst->width != src->width || dst->height != src->height)
+        return fail(MORPH_EINVAL, "dst is %d x %d but src is %d x %d", dst->width, dst->height,
+                    src->width, src->height);
+    if (overlap(packed_range(src), packed_range(dst))) return fail(MORPH_EINVAL, "dst overlaps src");
+    if (!mask) return fail(MORPH_EINVAL, "mask is NULL");
+    if (mw < 1 || mh < 1 || mw > MASK_MAX_SIDE || mh > MASK_MAX_SIDE)
+        return fail(MORPH_EINVAL, "mask %d x %d outside 1..%d", mw, mh, MASK_MAX_SIDE);
+    if (ox < 0 || ox >= mw || oy < 0 || oy >= mh)
+        return fail(MORPH_EINVAL, "origin (%d, %d) outside the %d x %d mask", ox, oy, mw, mh);
+    return MORPH_OK;
+}
+
+size_t mask_ws_bytes(int op, int W, int H, int nlev) {
+    size_t n = align256(mask_levels_bytes(W, H, nlev));
+    if (op == MORPH_OPEN || op == MORPH_CLOSE) n += align256((size_t)H * ((W + 31) / 32) * 4);
+    return n;
+}
+
 }  // namespace
 
 void set_error(const char *fmt, ...) {
@@ -362,6 +422,66 @@ size_t morph_workspace_size(int op, const morph_image *dst, const morph_image *s
         return packed_ws_bytes(op, src->width, src->height, se);
     }
     return rle_ws(op, src->width, src->height).total;
+}
+
+size_t morph_mask_workspace_size(int op, const morph_image *dst, const morph_image *src,
+                                 const uint8_t *mask, int mask_w, int mask_h, int origin_x,
+                                 int origin_y) {
+    if (check_mask_args(op, dst, src, mask, mask_w, mask_h, origin_x, origin_y)) return 0;
+    static thread_local MaskArgs a;
+    if (mask_runs(mask, mask_w, mask_h, origin_x, origin_y, false, a)) return 0;
+    return mask_ws_bytes(op, src->width, src->height, a.nlev);
+}
+
+morph_status morph_mask(int op, const morph_image *dst, const morph_image *src, const uint8_t *mask,
+                        int mask_w, int mask_h, int origin_x, int origin_y, void *workspace,
+                        size_t workspace_bytes, void *stream) {
+    morph_status st = check_mask_args(op, dst, src, mask, mask_w, mask_h, origin_x, origin_y);
+    if (st) return st;
+    static thread_local MaskArgs a;  // 8 KB: kept off the stack
+    const int W = src->width, H = src->height, nwv = (W + 31) / 32;
+    // stages: erosion by the element, or by the reflected one with complement
+    const bool two = op == MORPH_OPEN || op == MORPH_CLOSE;
+    const bool dil0 = op == MORPH_DILATE || op == MORPH_CLOSE;
+    if ((st = mask_runs(mask, mask_w, mask_h, origin_x, origin_y, dil0, a))) return st;
+    const size_t need = mask_ws_bytes(op, W, H, a.nlev);
+    if (need && (!workspace || workspace_bytes < need))
+        return fail(MORPH_ENOMEM, "the mask operation needs %zu bytes of workspace, got %zu", need,
+                    workspace ? workspace_bytes : (size_t)0);
+    if ((uintptr_t)workspace % 256) return fail(MORPH_EINVAL, "workspace is not 256-byte aligned");
+    uint32_t *levels = (uint32_t *)workspace;
+    uint32_t *mid = two ? (uint32_t *)((char *)workspace + align256(mask_levels_bytes(W, H, a.nlev)))
+                        : nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    a.W = W;
+    a.H = H;
+    a.nw_valid = nwv;
+    a.levels = levels;
+    a.src = (const uint32_t *)src->words;
+    a.sstride = src->stride_words * (word_bits(src->fmt) / 32);
+    a.inv_in = a.inv_out = dil0;
+    if (two) {
+        a.dst = mid;
+        a.dstride = nwv;
+        a.nw_cover = nwv;
+    } else {
+        a.dst = (uint32_t *)dst->words;
+        a.dstride = dst->stride_words * (word_bits(dst->fmt) / 32);
+        a.nw_cover = dst->fmt == MORPH_PACKED32 ? nwv : 2 * ((W + 63) / 64);
+    }
+    cudaError_t e = launch_mask_erode(a, s);
+    if (e == cudaSuccess && two) {
+        if ((st = mask_runs(mask, mask_w, mask_h, origin_x, origin_y, !dil0, a))) return st;
+        a.src = mid;
+        a.sstride = nwv;
+        a.dst = (uint32_t *)dst->words;
+        a.dstride = dst->stride_words * (word_bits(dst->fmt) / 32);
+        a.nw_cover = dst->fmt == MORPH_PACKED32 ? nwv : 2 * ((W + 63) / 64);
+        a.inv_in = a.inv_out = !dil0;
+        e = launch_mask_erode(a, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "mask morphology launch");
+    return MORPH_OK;
 }
 
 size_t morph_convert_workspace_size(int height) {

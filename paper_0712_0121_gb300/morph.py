@@ -81,6 +81,11 @@ def _load():
     lib.morph_rect.restype = ci
     lib.morph_workspace_size.argtypes = [ci, img_p, img_p, ci, ci, ci, ci]
     lib.morph_workspace_size.restype = sz
+    u8p = ctypes.POINTER(ctypes.c_uint8)
+    lib.morph_mask_workspace_size.argtypes = [ci, img_p, img_p, u8p, ci, ci, ci, ci]
+    lib.morph_mask_workspace_size.restype = sz
+    lib.morph_mask.argtypes = [ci, img_p, img_p, u8p, ci, ci, ci, ci, vp, sz, vp]
+    lib.morph_mask.restype = ci
     lib.morph_convert_workspace_size.argtypes = [ci]
     lib.morph_convert_workspace_size.restype = sz
     lib.rle_from_bitmap.argtypes = [img_p, img_p, vp, sz, vp]
@@ -287,6 +292,42 @@ def morph_open_rect(dst, src, se_w, se_h, origin_x=None, origin_y=None, workspac
 
 def morph_close_rect(dst, src, se_w, se_h, origin_x=None, origin_y=None, workspace=None, stream=None):
     morph_rect(CLOSE, dst, src, se_w, se_h, origin_x, origin_y, workspace, stream)
+
+
+def mask_workspace_size(op, dst, src, mask: np.ndarray, origin_x: int, origin_y: int) -> int:
+    m = _mask_bytes(mask)
+    return int(_lib.morph_mask_workspace_size(OPS.get(op, op), ctypes.byref(dst.desc()),
+                                              ctypes.byref(src.desc()),
+                                              m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                              m.shape[1], m.shape[0], origin_x, origin_y))
+
+
+def _mask_bytes(mask) -> np.ndarray:
+    m = np.ascontiguousarray(mask)
+    if m.ndim != 2:
+        raise ValueError("mask must be 2D")
+    return np.ascontiguousarray(m != 0, dtype=np.uint8)
+
+
+def morph_mask(op, dst: "Packed", src: "Packed", mask, origin_x=None, origin_y=None,
+               workspace: torch.Tensor | None = None, stream=None) -> None:
+    """Erode / dilate / open / close packed ``src`` into ``dst`` by an
+    arbitrary structuring element ``mask`` (2D array, nonzero = in the
+    element).  Origin defaults to the centre (mask_w // 2, mask_h // 2).  A
+    workspace is allocated here when none is given."""
+    m = _mask_bytes(mask)
+    mh, mw = m.shape
+    ox = mw // 2 if origin_x is None else origin_x
+    oy = mh // 2 if origin_y is None else origin_y
+    opc = OPS.get(op, op)
+    if workspace is None:
+        n = mask_workspace_size(opc, dst, src, m, ox, oy)
+        if n:
+            workspace = torch.empty(n, dtype=torch.uint8, device=src.words.device)
+    wp, wn = _ws_args(workspace)
+    _check(_lib.morph_mask(opc, ctypes.byref(dst.desc()), ctypes.byref(src.desc()),
+                           m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), mw, mh, ox, oy, wp, wn,
+                           _stream_handle(stream)))
 
 
 def rle_rect_noalloc(op, dst: "Rle", src: "Rle", se_w: int, se_h: int, origin_x=None,

@@ -132,7 +132,7 @@ __device__ bool wait_count(const int *ctr, int target, int *abort_flag, int *sta
 // {none, reach<=1, halo 1, 2, 4 words}.
 template <int NST, bool HS, int KMAX, int HALO, bool HX1>
 __device__ __noinline__ void tile_fn(const PackedArgs &a, int bx, int by, uint32_t *sm) {
-    packed_tile<NST, HS, KMAX, HALO, HX1>(a, bx, by, sm);
+    packed_tile<NST, HS, KMAX, HALO, HX1, false>(a, bx, by, sm);
 }
 
 template <int NST, int KMAX>
@@ -504,7 +504,7 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
                 return BATCH_KMAX[batch_kidx(packed_kmax(t))];
             }();
             if (packed_plan(a, q.op, c.sw, c.sh, c.ox, c.oy, q.tile_rows ? q.tile_rows : tile_rows,
-                            MAX_THREADS, kmax_class) != 0)
+                            MAX_THREADS, kmax_class, false) != 0)
                 return berr(MORPH_EINVAL, "rectangle reaches more than 128 pixels sideways", j);
             b.variant = packed_variant(a);
             const dim3 g = packed_grid(a);

@@ -74,14 +74,17 @@ struct PackedArgs {
     int nstrips;
     int slot_words;       // smem words per group row slot
     int nwt;              // u32 words per thread
+    int ring;             // 1: ring tile (cp.async row slots), 0: register-prefetch tile
     int vec;              // vector loads / stores of a thread's words allowed (aligned bases and strides)
 };
 
 int packed_halo(int sw, int ex);   // register-window halo words of the H stage (0: too wide)
 // kmax_class: the column-counter planes of the kernel set that will run the
 // plan (the batch kernel instantiates fewer classes); -1 = packed_kmax().
+// ring2: open / close use the ring tile (the batch kernel, with two CTAs
+// per SM, runs them faster on the register-prefetch tile).
 int packed_plan(PackedArgs &a, int op, int sw, int sh, int ox, int oy, int band_rows_hint,
-                int block_threads_hint, int kmax_class = -1);
+                int block_threads_hint, int kmax_class = -1, bool ring2 = true);
 size_t packed_smem_bytes(const PackedArgs &a);
 int packed_kmax(const PackedArgs &a);
 int packed_threads(const PackedArgs &a);

@@ -80,8 +80,11 @@ int packed_kmax(const PackedArgs &a) {
 
 size_t packed_smem_bytes(const PackedArgs &a) {
     if (!a.hmode) return 0;
-    if (a.nst == 1) return (size_t)PK_NBUF1 * pk1_rb(a.nwt) * a.groups * a.slot_words * sizeof(uint32_t);
-    return (size_t)a.nst * 2 * a.rb * a.groups * a.slot_words * sizeof(uint32_t);
+    if (!a.ring) return (size_t)a.nst * 2 * a.rb * a.groups * a.slot_words * sizeof(uint32_t);
+    // ring tile: PK_NBUF1 chunks of input rows, plus one chunk of first-stage
+    // rows for open / close
+    return (size_t)(PK_NBUF1 + (a.nst == 2 ? 1 : 0)) * pk1_rb(a.nwt) * a.groups * a.slot_words *
+           sizeof(uint32_t);
 }
 
 int packed_threads(const PackedArgs &a) { return ((a.groups * a.tpr + 31) / 32) * 32; }
@@ -93,7 +96,7 @@ dim3 packed_grid(const PackedArgs &a) {
 // Fill the stage and tiling parameters.  Returns 0 on success, -1 if the
 // rectangle is too wide for the horizontal register window.
 int packed_plan(PackedArgs &a, int op, int sw, int sh, int ox, int oy, int band_hint,
-                int threads_hint, int kmax_class) {
+                int threads_hint, int kmax_class, bool ring2) {
     const int rx = sw - 1 - ox, ry = sh - 1 - oy;
     a.sw = sw;
     a.sh = sh;
@@ -118,9 +121,10 @@ int packed_plan(PackedArgs &a, int op, int sw, int sh, int ox, int oy, int band_
     int max_threads = threads_hint > 0 ? threads_hint : MAX_THREADS;
     if (max_threads > MAX_THREADS) max_threads = MAX_THREADS;
     if (max_threads < 32) max_threads = 32;
-    // words per thread: the one-stage tile picks 2 or 4 (see pk1_nwt), the
-    // two-stage tile moves 2
-    const bool one_stage = a.nst == 1 && a.hmode;
+    // words per thread: the ring tile (sw > 1) picks 2 or 4 (see pk1_nwt),
+    // the register-prefetch tile moves 2
+    const bool one_stage = a.hmode != 0 && (a.nst == 1 || ring2);  // ring tile
+    a.ring = one_stage;
     const bool hx1 = sw <= 3 && a.ex[0] <= 1 && sw - 1 - a.ex[0] <= 1;
     const int nwt = one_stage ? pk1_nwt(hx1, kmax_class >= 0 ? kmax_class : packed_kmax(a)) : PK_NWT;
     a.nwt = nwt;

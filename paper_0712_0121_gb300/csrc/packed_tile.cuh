@@ -276,7 +276,7 @@ __device__ __forceinline__ void lds_window(const uint32_t *own, uint32_t (&v)[NW
     }
 }
 
-template <int NWT, int KMAX, int HALO, bool HX1>
+template <int NST, int NWT, int KMAX, int HALO, bool HX1>
 __device__ __forceinline__ void packed1_tile(const PackedArgs &a, int bx, int by, uint32_t *sm) {
     constexpr int RB = pk1_rb(NWT), NBUF = PK_NBUF1;
     constexpr int PAD = pk1_pad(HALO, NWT), NWIN = NWT + 2 * HALO;
@@ -284,7 +284,7 @@ __device__ __forceinline__ void packed1_tile(const PackedArgs &a, int bx, int by
     using WT = WordsT<NWT>;
     // the plan's layout (threads per row, slot size, shared memory) is made
     // for a.nwt words per thread; never run this body on another layout
-    if (a.nwt != NWT) return;
+    if (a.nwt != NWT || !a.ring) return;
     const int tid = threadIdx.x;
     const int tpr = a.tpr, groups = a.groups, band = a.band, H = a.H;
     const int g = tid / tpr, lt = tid - g * tpr;
@@ -293,7 +293,8 @@ __device__ __forceinline__ void packed1_tile(const PackedArgs &a, int bx, int by
     const int strip0 = by * a.strip_words;
     const int w0 = strip0 - a.halo_words + lt * NWT;
     const int Y0 = (bx * groups + gg) * band;
-    const int wup = a.sh - 1;
+    const int sh = a.sh;
+    const int wup = NST * (sh - 1);
     const int iters = band + wup;
     const int y_end = min(Y0 + band, H);
     const int K = a.K;
@@ -301,6 +302,7 @@ __device__ __forceinline__ void packed1_tile(const PackedArgs &a, int bx, int by
 #pragma unroll
     for (int k = 0; k < KC; ++k) eqm[k] = a.eqm[k];
     const HPlan hp = make_hplan(a.sw, a.ex[0]);
+    const HPlan hp2 = make_hplan(a.sw, a.ex[1]);
     const uint32_t inm_in = a.inv_in ? ONES : 0u, inm_out = a.inv_out ? ONES : 0u;
 
     // stage-input masks of the window words: padding bits and words outside
@@ -326,17 +328,22 @@ __device__ __forceinline__ void packed1_tile(const PackedArgs &a, int bx, int by
     // a.vec: bases aligned to NWT words and strides multiples of NWT words
     const bool vec_ld = a.vec && all_ld;
     const bool vec_st = a.vec && all_st;
-    ColCounter<KC> cc[NWT];
+    ColCounter<KC> cc[NWT], cc2[NWT];
 #pragma unroll
-    for (int t = 0; t < NWT; ++t) cc[t].reset();
+    for (int t = 0; t < NWT; ++t) {
+        cc[t].reset();
+        cc2[t].reset();
+    }
 
-    const int r_first = Y0 - a.ey[0];
+    const int r_first = Y0 - (NST == 2 ? a.ey[1] : 0) - a.ey[0];
     const int64_t sstride = a.sstride, dstride = a.dstride;
     const uint32_t *src = a.src + w0;  // dereferenced only for words inside the row
     uint32_t *dst = a.dst + w0;
     const int row_words = groups * a.slot_words;       // between row slots of a chunk
     const int buf_words = RB * row_words;              // between chunks
     uint32_t *my = sm + gg * a.slot_words + PAD + lt * NWT;  // own words, row 0, buffer 0
+    // two stages: the first stage's rows are exchanged through RB more slots
+    uint32_t *xmy = my + NBUF * buf_words;
 
     auto issue = [&](int c) {
         if (act) {
@@ -364,6 +371,30 @@ __device__ __forceinline__ void packed1_tile(const PackedArgs &a, int bx, int by
         cp_async_commit();
     };
 
+    auto store_out = [&](int it, const uint32_t (&h)[NWT]) {
+        const int y = Y0 + it - wup;
+        if (it >= wup && y < y_end) {
+            uint32_t o[NWT];
+#pragma unroll
+            for (int t = 0; t < NWT; ++t) o[t] = (h[t] ^ inm_out) & vmask[t];
+            uint32_t *p = dst + (int64_t)y * dstride;
+            if (vec_st) {
+                typename WT::V x;
+                x.x = o[0];
+                x.y = o[1];
+                if constexpr (NWT == 4) {
+                    x.z = o[2];
+                    x.w = o[3];
+                }
+                *reinterpret_cast<typename WT::V *>(p) = x;
+            } else {
+#pragma unroll
+                for (int t = 0; t < NWT; ++t)
+                    if (st_ok[t]) p[t] = o[t];
+            }
+        }
+    };
+
     const int nch = (iters + RB - 1) / RB;
     issue(0);
     if (nch > 1) issue(1);
@@ -387,26 +418,39 @@ __device__ __forceinline__ void packed1_tile(const PackedArgs &a, int bx, int by
 #pragma unroll
                 for (int t = 0; t < NWT; ++t) h[t] = cc[t].push(h[t], K, eqm);
             }
-            const int y = Y0 + it - wup;
-            if (it >= wup && y < y_end) {
-                uint32_t o[NWT];
-#pragma unroll
-                for (int t = 0; t < NWT; ++t) o[t] = (h[t] ^ inm_out) & vmask[t];
-                uint32_t *p = dst + (int64_t)y * dstride;
-                if (vec_st) {
-                    typename WT::V x;
-                    x.x = o[0];
-                    x.y = o[1];
-                    if constexpr (NWT == 4) {
-                        x.z = o[2];
-                        x.w = o[3];
-                    }
-                    *reinterpret_cast<typename WT::V *>(p) = x;
-                } else {
-#pragma unroll
-                    for (int t = 0; t < NWT; ++t)
-                        if (st_ok[t]) p[t] = o[t];
+            if constexpr (NST == 2) {
+                // second stage input: the complement of the first stage's row
+                // (dilation by duality), 1 outside the image and in padding bits
+                const int y1 = Y0 - a.ey[1] + it - (sh - 1);
+                const uint32_t fill = (y1 >= 0 && y1 < H) ? 0u : ONES;
+                typename WT::V x;
+                x.x = ~(h[0] & vmask[0]) | fill;
+                x.y = ~(h[1] & vmask[1]) | fill;
+                if constexpr (NWT == 4) {
+                    x.z = ~(h[2] & vmask[2]) | fill;
+                    x.w = ~(h[3] & vmask[3]) | fill;
                 }
+                if (act) *reinterpret_cast<typename WT::V *>(xmy + i * row_words) = x;
+            } else {
+                store_out(it, h);
+            }
+        }
+        if constexpr (NST == 2) {
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < RB; ++i) {
+                const int it = c * RB + i;
+                uint32_t v[NWIN];
+                lds_window<NWT, HALO>(xmy + i * row_words, v);
+#pragma unroll
+                for (int j = 0; j < NWIN; ++j) v[j] |= nmw[j];
+                uint32_t h[NWT];
+                h_stage_win<NWT, HALO, HX1>(v, h, hp2);
+                if (KMAX > 0 && it >= sh - 1) {
+#pragma unroll
+                    for (int t = 0; t < NWT; ++t) h[t] = cc2[t].push(h[t], K, eqm);
+                }
+                store_out(it, h);
             }
         }
     }
@@ -420,6 +464,7 @@ __device__ __forceinline__ void packed1_tile(const PackedArgs &a, int bx, int by
 template <int NST, bool HS, int KMAX, int HALO, bool HX1>
 __device__ __forceinline__ void packed_tile2(const PackedArgs &a, int bx, int by, uint32_t *sm) {
     constexpr int NWT = PK_NWT;
+    if (a.ring || a.nwt != NWT) return;  // a plan made for the ring tile
     constexpr int RB = PK_RB;
     constexpr int PAD = pk_pad(HALO);
     constexpr int KC = KMAX > 0 ? KMAX : 1;
@@ -637,10 +682,12 @@ __device__ __forceinline__ void packed_tile2(const PackedArgs &a, int bx, int by
     }
 }
 
-template <int NST, bool HS, int KMAX, int HALO, bool HX1>
+// RING2: open / close on the ring tile (else the register-prefetch tile);
+// the plan's a.ring must agree.
+template <int NST, bool HS, int KMAX, int HALO, bool HX1, bool RING2 = true>
 __device__ __forceinline__ void packed_tile(const PackedArgs &a, int bx, int by, uint32_t *sm) {
-    if constexpr (NST == 1 && HS) {
-        packed1_tile<pk1_nwt(HX1, KMAX), KMAX, HALO, HX1>(a, bx, by, sm);
+    if constexpr (HS && (NST == 1 || RING2)) {
+        packed1_tile<NST, pk1_nwt(HX1, KMAX), KMAX, HALO, HX1>(a, bx, by, sm);
     } else {
         packed_tile2<NST, HS, KMAX, HALO, HX1>(a, bx, by, sm);
     }

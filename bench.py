@@ -193,13 +193,18 @@ def whole_job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
     return units_per_rank * world / (ms_max * 1e-3)
 
 
+# Sources the batch kernel and its planner are built from (the entry points
+# of the single-image operations, masks and the no-alloc path are not).
+BATCH_SOURCES = ("batch.cu", "packed.cu", "rle.cu", "morph_internal.cuh", "packed_tile.cuh",
+                 "rle_tile.cuh", "counters.cuh", "cp_async.cuh")
+
+
 def csrc_digest():
-    """SHA-256 over the CUDA sources and the ABI header (ties a profile
-    record to the kernels it was taken from)."""
-    import glob
+    """SHA-256 over the sources of the batch kernel and the ABI header (ties
+    a profile record of that kernel to the code it was taken from)."""
     import hashlib
     h = hashlib.sha256()
-    files = sorted(glob.glob(os.path.join(ROOT, "paper_0712_0121_gb300", "csrc", "*.cu*")))
+    files = [os.path.join(ROOT, "paper_0712_0121_gb300", "csrc", f) for f in BATCH_SOURCES]
     files.append(os.path.join(ROOT, "include", "morph.h"))
     for f in files:
         with open(f, "rb") as fh:

@@ -28,10 +28,16 @@ def _key(W, H, op, se):
 
 
 class Tuner:
-    def __init__(self, cache_path=None, pages_per_class=8, reps=3):
+    """``min_pixels``: every timed batch repeats the class's pages until it
+    holds at least this many pixels, so that both paths are timed at full
+    occupancy (a few pages leave most CTAs idle on the packed path, whose
+    tiles are few and large, and time latency instead of throughput)."""
+
+    def __init__(self, cache_path=None, pages_per_class=8, reps=3, min_pixels=1_000_000_000):
         self.cache_path = cache_path
         self.pages_per_class = pages_per_class
         self.reps = reps
+        self.min_pixels = min_pixels
         self.table = {}
         if cache_path and os.path.exists(cache_path):
             with open(cache_path) as f:
@@ -72,7 +78,8 @@ class Tuner:
         n = self.pages_per_class
         pages = {d: self._pages(W, H, d, n) for d in densities}
         mid = self._pages(W, H, 0.08, n)
-        outs = [M.Packed.empty(W, H, 64) for _ in range(n)]
+        total = n * max(1, -(-self.min_pixels // (n * W * H)))
+        outs = [M.Packed.empty(W, H, 64) for _ in range(total)]
         for op in ops:
             for se in ses:
                 self.tune_class(W, H, op, se, densities, bands, pages, mid, outs)
@@ -83,26 +90,28 @@ class Tuner:
         """Measure one (size, op, rectangle) class; returns its table entry."""
         from . import morph as M
         n = self.pages_per_class
+        total = n * max(1, -(-self.min_pixels // (n * W * H)))  # page-ops per timed batch
         entry = {"density": [], "packed_ms": [], "rle_ms": [], "band": None}
         mid = mid if mid is not None else self._pages(W, H, 0.08, n)
-        outs = outs if outs is not None else [M.Packed.empty(W, H, 64) for _ in range(n)]
+        if outs is None or len(outs) < total:
+            outs = [M.Packed.empty(W, H, 64) for _ in range(total)]
+
+        def jobs_of(srcs, **kw):
+            return [dict(op=op, se=se, src=srcs[k % n], dst=outs[k], **kw) for k in range(total)]
+
         best_band, best_t = 0, float("inf")
         for band in bands:
-            jobs = [dict(op=op, se=se, path="packed", src=s, dst=d, tile_rows=band)
-                    for s, d in zip(mid, outs)]
-            t = self._time_batch(jobs, self.reps)
+            t = self._time_batch(jobs_of(mid, path="packed", tile_rows=band), self.reps)
             if t < best_t:
                 best_band, best_t = band, t
         entry["band"] = best_band
         for dens in densities:
             pg = pages[dens] if pages is not None else self._pages(W, H, dens, n)
-            tp = self._time_batch([dict(op=op, se=se, path="packed", src=s, dst=d, tile_rows=best_band)
-                                   for s, d in zip(pg, outs)], self.reps)
-            tr = self._time_batch([dict(op=op, se=se, path="rle", src=s, dst=d)
-                                   for s, d in zip(pg, outs)], self.reps)
+            tp = self._time_batch(jobs_of(pg, path="packed", tile_rows=best_band), self.reps)
+            tr = self._time_batch(jobs_of(pg, path="rle"), self.reps)
             entry["density"].append(dens)
-            entry["packed_ms"].append(tp / n)
-            entry["rle_ms"].append(tr / n)
+            entry["packed_ms"].append(tp / total)
+            entry["rle_ms"].append(tr / total)
         self.table[_key(W, H, op, se)] = entry
         return entry
 

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "mask.cuh"
 #include "morph_internal.cuh"
 
 namespace morph {
@@ -440,7 +441,7 @@ morph_status morph_mask(int op, const morph_image *dst, const morph_image *src, 
     if (st) return st;
     static thread_local MaskArgs a;  // 8 KB: kept off the stack
     const int W = src->width, H = src->height, nwv = (W + 31) / 32;
-    // stages: erosion by the element, or by the reflected one with complement
+    // stages: erosion by the element (AND) or dilation by the reflected one (OR)
     const bool two = op == MORPH_OPEN || op == MORPH_CLOSE;
     const bool dil0 = op == MORPH_DILATE || op == MORPH_CLOSE;
     if ((st = mask_runs(mask, mask_w, mask_h, origin_x, origin_y, dil0, a))) return st;
@@ -459,7 +460,7 @@ morph_status morph_mask(int op, const morph_image *dst, const morph_image *src, 
     a.levels = levels;
     a.src = (const uint32_t *)src->words;
     a.sstride = src->stride_words * (word_bits(src->fmt) / 32);
-    a.inv_in = a.inv_out = dil0;
+    a.use_or = dil0;
     if (two) {
         a.dst = mid;
         a.dstride = nwv;
@@ -469,7 +470,7 @@ morph_status morph_mask(int op, const morph_image *dst, const morph_image *src, 
         a.dstride = dst->stride_words * (word_bits(dst->fmt) / 32);
         a.nw_cover = dst->fmt == MORPH_PACKED32 ? nwv : 2 * ((W + 63) / 64);
     }
-    cudaError_t e = launch_mask_erode(a, s);
+    cudaError_t e = launch_mask_stage(a, s);
     if (e == cudaSuccess && two) {
         if ((st = mask_runs(mask, mask_w, mask_h, origin_x, origin_y, !dil0, a))) return st;
         a.src = mid;
@@ -477,8 +478,8 @@ morph_status morph_mask(int op, const morph_image *dst, const morph_image *src, 
         a.dst = (uint32_t *)dst->words;
         a.dstride = dst->stride_words * (word_bits(dst->fmt) / 32);
         a.nw_cover = dst->fmt == MORPH_PACKED32 ? nwv : 2 * ((W + 63) / 64);
-        a.inv_in = a.inv_out = !dil0;
-        e = launch_mask_erode(a, s);
+        a.use_or = !dil0;
+        e = launch_mask_stage(a, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "mask morphology launch");
     return MORPH_OK;

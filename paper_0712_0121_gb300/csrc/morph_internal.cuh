@@ -146,35 +146,6 @@ size_t vpass_smem_bytes(const VArgs &a);
 bool vband_plan(VArgs &a, int W, int H, int sh, size_t smem_budget);
 size_t vband_smem_bytes(const VArgs &a);
 int vband_grid(const VArgs &a);
-// ------------------------------------------------------ arbitrary masks
-// Erosion stage by an arbitrary element given as horizontal runs (see
-// mask.cu).  A run of width w at element row j, columns [x0, x0 + w), with
-// origin (ox, oy): dy = j - oy, m = floor(log2 w), dx1 = x0 - ox,
-// dx2 = dx1 + w - 2^m.
-constexpr int MASK_MAX_RUNS = 1024;
-constexpr int MASK_MAX_SIDE = 4096;   // element width and height limit
-constexpr int MASK_MAX_LEVELS = 12;   // floor(log2(MASK_MAX_SIDE))
-struct MaskRun {
-    int16_t dy, dx1, dx2, m;
-};
-struct MaskArgs {
-    const uint32_t *src;
-    int64_t sstride;          // u32 words between source rows
-    uint32_t *dst;
-    int64_t dstride;          // u32 words between destination rows
-    int nw_cover;             // u32 words written per destination row
-    int W, H, nw_valid;
-    int inv_in, inv_out;      // complement input / output (dilation by duality)
-    uint32_t *levels;         // doubling levels 1..nlev, rows of nw_valid words
-    int nlev, nruns;
-    MaskRun runs[MASK_MAX_RUNS];
-};
-// Words kept left of a level row: A_2^m at positions down to -(2^m - 1)
-// still reaches the image.
-__host__ __device__ inline int mask_pad_words(int nlev) { return ((1 << nlev) - 1 + 31) / 32; }
-size_t mask_levels_bytes(int W, int H, int nlev);
-cudaError_t launch_mask_erode(const MaskArgs &a, cudaStream_t s);
-
 constexpr size_t VBAND_SMEM_BUDGET = 96 * 1024;
 // Runs per staging buffer of the band tile (two buffers).
 constexpr int VBAND_RUN_CHUNK = 2048;

@@ -39,7 +39,8 @@ OPS = ["open", "close"]
 METRIC = "Gpix/s rect erode/dilate (packed, RLE) vs HBM peak; batched pages/s; p50/p99 ms"
 UNIT = "Gpix/s"
 WORKLOAD = ("letter-300dpi: 2550x3300 text pages, open+close x {3,7,15,31,51 squares, "
-            "1x51, 51x1}, packed and RLE paths, one persistent batch launch per step")
+            "1x51, 51x1}, packed and RLE paths (a page's RLE jobs share one bitmap->RLE "
+            "encode per step), one persistent batch launch per step")
 
 
 def env_rank():

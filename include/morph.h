@@ -240,7 +240,10 @@ MORPH_API morph_status rle_to_bitmap(const morph_image *dst_packed, const morph_
  * (bounded spin, acquire loads) only for items of smaller index, which are
  * already held by running CTAs, so the launch cannot deadlock.  A wait longer
  * than the plan's limit (4 s) latches MORPH_ETIMEOUT and stops every CTA; an RLE buffer that is
- * too small latches MORPH_ECAPACITY and leaves that job's dst unwritten.
+ * too small latches MORPH_ECAPACITY and leaves that job's dst unwritten (and, when it is the
+ * buffer of a shared source encode, the dst of every job sharing it).  RLE-path jobs without
+ * depends_on that read the same source page (same words, stride, format and size) share one
+ * bitmap -> RLE encode of it: the first such job encodes, the others read its runs.
  *
  * tile_rows: for jobs whose own tile_rows is 0, the row-band height of
  * packed tiles and the rows per work item of RLE-path and MORPH_TO_RLE jobs

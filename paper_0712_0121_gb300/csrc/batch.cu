@@ -20,6 +20,7 @@
 // launch can be captured in a CUDA graph and replayed.
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -31,6 +32,22 @@ namespace {
 
 constexpr uint32_t PLAN_MAGIC = 0x4d425031u;  // "MBP1"
 constexpr int MAX_PH = 11;
+// Phases of the bitmap -> runs encode that starts an RLE-path job.
+constexpr int ENCODE_PHASES = 3;
+
+struct SrcKey {  // a source page, for sharing its encode between jobs
+    const void *words;
+    int64_t stride;
+    int fmt, W, H;
+    bool operator<(const SrcKey &o) const {
+        if (words != o.words) return words < o.words;
+        if (stride != o.stride) return stride < o.stride;
+        if (fmt != o.fmt) return fmt < o.fmt;
+        if (W != o.W) return W < o.W;
+        return H < o.H;
+    }
+};
+
 // Rows per row-range item (bitmap <-> runs, row pass, runs -> bitmap): a
 // multiple of 64 up to 1024, chosen per job at plan time.
 constexpr int BATCH_ROWS_MIN = 64, BATCH_ROWS_MAX = 1024;
@@ -77,6 +94,9 @@ struct BatchJob {
     VArgs va[2];                // pointers are filled on the device from ws offsets
     int32_t vkind[2];           // between-line variant (nwt, kmax)
     int64_t off_counts, off_rpA, off_runsA, off_rpB, off_runsB, off_nA, off_nB, off_bmp;
+    int64_t off_srp, off_sruns;  // the RLE source the first stage reads (own A, or a shared one)
+    int32_t src_job;             // job whose encode produced that source (itself if not shared)
+    int32_t dep_phase;           // phase of `dep` whose completion gates this job's phase 0
     int64_t cap;                // runs capacity of each RLE buffer
     int rows;                   // rows per row-range item
 };
@@ -229,8 +249,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batch(const uint8_t *plan,
                                 (unsigned long long)hdr->wait_limit_ns);
             } else if (J.dep >= 0) {
                 const BatchJob &D = jobs[J.dep];
-                ok = wait_count(done + (size_t)J.dep * MAX_PH + D.nphase - 1,
-                                D.phase_items[D.nphase - 1], &ctrl->abort_flag, status,
+                ok = wait_count(done + (size_t)J.dep * MAX_PH + J.dep_phase,
+                                D.phase_items[J.dep_phase], &ctrl->abort_flag, status,
                                 (unsigned long long)hdr->wait_limit_ns);
             }
             s_ok = ok;
@@ -240,7 +260,10 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batch(const uint8_t *plan,
         if (!s_ok) break;
         __threadfence();
 
-        const bool ovf = it.phase > 0 && *(volatile int *)(overflow + it.job) != 0;
+        // overflow: bit 0 = one of the job's RLE buffers, bit 1 = its source
+        // encode (which jobs sharing that encode check too)
+        const bool ovf = (it.phase > 0 && *(volatile int *)(overflow + it.job) != 0) ||
+                         (J.src_job != it.job && (*(volatile int *)(overflow + J.src_job) & 2));
         switch (it.kind) {
         case IK_PACKED:
             run_packed_tile(J.variant, J.pa, it.idx % J.gx, it.idx / J.gx, sm);
@@ -268,16 +291,16 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batch(const uint8_t *plan,
             int64_t *nr = reinterpret_cast<int64_t *>(ws + (toA ? J.off_nA : J.off_nB));
             scan_rows_block(reinterpret_cast<const int32_t *>(ws + J.off_counts), J.H, rp, nr, J.cap,
                             status);
-            if (threadIdx.x == 0 && rp[J.H] > J.cap) atomicExch(overflow + it.job, 1);
+            if (threadIdx.x == 0 && rp[J.H] > J.cap) atomicOr(overflow + it.job, st < 0 ? 3 : 1);
             break;
         }
         case IK_ROW_COUNT:
         case IK_ROW_WRITE: {
             if (ovf) break;
             const int st = J.phase_stage[it.phase];
-            const bool fromA = st == 0;
-            const RleIn in{reinterpret_cast<const int32_t *>(ws + (fromA ? J.off_rpA : J.off_rpB)),
-                           reinterpret_cast<const uint16_t *>(ws + (fromA ? J.off_runsA : J.off_runsB)),
+            const bool fromA = st == 0;  // stage 0 reads the source, writes B; stage 1 B -> A
+            const RleIn in{reinterpret_cast<const int32_t *>(ws + (fromA ? J.off_srp : J.off_rpB)),
+                           reinterpret_cast<const uint16_t *>(ws + (fromA ? J.off_sruns : J.off_runsB)),
                            J.W, J.H};
             const int r0 = it.idx * J.rows;
             const bool write = it.kind == IK_ROW_WRITE;
@@ -292,8 +315,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batch(const uint8_t *plan,
             const int st = J.phase_stage[it.phase];
             const bool fromA = st == 0;
             VArgs va = J.va[st];
-            va.in.row_ptr = reinterpret_cast<const int32_t *>(ws + (fromA ? J.off_rpA : J.off_rpB));
-            va.in.runs = reinterpret_cast<const uint16_t *>(ws + (fromA ? J.off_runsA : J.off_runsB));
+            va.in.row_ptr = reinterpret_cast<const int32_t *>(ws + (fromA ? J.off_srp : J.off_rpB));
+            va.in.runs = reinterpret_cast<const uint16_t *>(ws + (fromA ? J.off_sruns : J.off_runsB));
             if (st == J.nst - 1) {
                 // last stage: the rows go straight to the job's packed output
                 va.bmp = J.dst;
@@ -425,6 +448,7 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
     };
     int64_t off = al(sizeof(Ctrl) + (size_t)n * MAX_PH * sizeof(int) + (size_t)n * sizeof(int));
     ws_ctrl = off;
+    std::map<SrcKey, int> encoders;  // source page -> job that encodes it to runs
     for (int j = 0; j < n; ++j) {
         const morph_job &q = jobs[j];
         BatchJob &b = J[j];
@@ -435,6 +459,8 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
         if (q.depends_on < -1 || q.depends_on >= j)
             return berr(MORPH_EINVAL, "depends_on must be -1 or an earlier job", j);
         b.dep = q.depends_on;
+        b.dep_phase = b.dep >= 0 ? J[b.dep].nphase - 1 : 0;
+        b.src_job = j;
         if (q.op == MORPH_TO_RLE) {
             if (!packed(s) || d.fmt != MORPH_RLE) return berr(MORPH_EINVAL, "MORPH_TO_RLE needs a packed src and an RLE dst", j);
             if (s.width < 1 || s.height < 1 || s.width != d.width || s.height != d.height || s.width > 65535)
@@ -528,13 +554,39 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
             const int rpr = rle_runs_per_row > 0 ? rle_runs_per_row : W / 16 + 4;
             b.cap = (int64_t)H * (rpr < (W + 1) / 2 ? rpr : (W + 1) / 2);
             if (b.cap < 1) b.cap = 1;
+            // Jobs on the same source page share one bitmap -> RLE encode: the
+            // first eligible job encodes into its buffer A (which it then
+            // only reads), later ones read that buffer and wait for its
+            // encode phases instead of encoding again.  Only jobs without a
+            // user dependency share, and only encoders whose A stays intact
+            // (a two-stage run pass writes its second stage into A).
+            const bool a_rewritten = b.nst == 2 && c.sh == 1;
+            int enc = -1;
+            if (q.depends_on < 0) {
+                const SrcKey key{s.words, s.stride_words, s.fmt, W, H};
+                auto f = encoders.find(key);
+                if (f != encoders.end()) enc = f->second;
+                else if (!a_rewritten) encoders[key] = j;
+            }
             b.off_counts = off; off += al((size_t)H * 4);
             b.off_nA = off; off += al(8);
             b.off_nB = off; off += al(8);
-            b.off_rpA = off; off += al((size_t)(H + 1) * 4);
             b.off_rpB = off; off += al((size_t)(H + 1) * 4);
-            b.off_runsA = off; off += al((size_t)b.cap * 4);
             b.off_runsB = off; off += al((size_t)b.cap * 4);
+            if (enc < 0 || a_rewritten) {
+                b.off_rpA = off; off += al((size_t)(H + 1) * 4);
+                b.off_runsA = off; off += al((size_t)b.cap * 4);
+            }
+            if (enc >= 0) {
+                b.src_job = enc;
+                b.dep = enc;
+                b.dep_phase = ENCODE_PHASES - 1;
+                b.off_srp = J[enc].off_rpA;
+                b.off_sruns = J[enc].off_runsA;
+            } else {
+                b.off_srp = b.off_rpA;
+                b.off_sruns = b.off_runsA;
+            }
             if (b.nst == 2 && c.sh > 1) {
                 b.off_bmp = off;
                 off += al((size_t)H * ((W + 31) / 32) * 4);
@@ -548,9 +600,11 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
                 b.phase_stage[p] = stage;
                 ++p;
             };
-            add(IK_B2R_COUNT, rows_items, -1);
-            add(IK_SCAN, 1, -1);
-            add(IK_B2R_WRITE, rows_items, -1);
+            if (b.src_job == j) {  // encode the source: ENCODE_PHASES phases
+                add(IK_B2R_COUNT, rows_items, -1);
+                add(IK_SCAN, 1, -1);
+                add(IK_B2R_WRITE, rows_items, -1);
+            }
             for (int st = 0; st < b.nst; ++st) {
                 // stage order: open = erode then dilate; close = dilate then erode
                 const bool dil = (q.op == MORPH_DILATE) || (q.op == MORPH_OPEN && st == 1) ||
@@ -613,7 +667,7 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
     I.clear();
     int maxlevel = 0;
     for (int j = 0; j < n; ++j) {
-        J[j].level0 = J[j].dep >= 0 ? J[J[j].dep].level0 + J[J[j].dep].nphase : 0;
+        J[j].level0 = J[j].dep >= 0 ? J[J[j].dep].level0 + J[j].dep_phase + 1 : 0;
         const int top = J[j].level0 + J[j].nphase;
         if (top > maxlevel) maxlevel = top;
     }

@@ -115,3 +115,46 @@ def test_config4_like_sample():
     M.Batch(jobs).launch()
     assert M.sync_status() == M.MORPH_OK
     check_all(jobs, imgs)
+
+
+def test_rle_jobs_on_one_page_share_its_encode():
+    """RLE-path jobs on the same source page encode it once: every job, the
+    encoder and the jobs that read its runs (including two-stage run passes,
+    which write their second stage into their own buffer), is exact."""
+    W, H = 700, 450
+    img = synth.text_page(W, H, 4242, 0.15, glyph=(4, 12, 6, 14), gap=(2, 6), ncols=2)[0]
+    src = M.pack(img, 64)
+    ops = [("open", (1, 1)), ("close", (9, 1)), ("open", (1, 7)), ("erode", (5, 5)), ("close", (31, 3)),
+           ("dilate", (15, 15)), ("open", (41, 1)), ("close", (3, 3))]
+    jobs = []
+    for op, se in ops:
+        dst = M.Packed.empty(W, H, 64)
+        dst.words.fill_(-1)
+        jobs.append(dict(op=op, se=se, path="rle", src=src, dst=dst))
+    pdst = M.Packed.empty(W, H, 64)
+    jobs.append(dict(op="close", se=(7, 7), path="packed", src=src, dst=pdst))
+    b = M.Batch(jobs)
+    for _ in range(2):  # a relaunch recomputes the shared encode
+        b.launch()
+        assert M.sync_status() == M.MORPH_OK
+        for j in jobs:
+            sw, sh = j["se"]
+            ref = oracle.apply(j["op"], img, sw, sh, mode="separable", threads=NCORES)
+            assert np.array_equal(unpack_words(j["dst"].words, W), ref), (j["op"], j["se"], j["path"])
+
+
+def test_shared_encode_overflow_is_reported():
+    W, H = 400, 100
+    img = synth.random_bits((H, W), 99, 0.5)
+    src = M.pack(img, 64)
+    jobs = [dict(op=op, se=(3, 3), path="rle", src=src, dst=M.Packed.empty(W, H, 64))
+            for op in ("open", "close", "erode")]
+    b = M.Batch(jobs, rle_runs_per_row=2)
+    b.launch()
+    assert M.sync_status() == M.MORPH_ECAPACITY
+    ok = M.Batch(jobs, rle_runs_per_row=W // 2 + 1)  # room for any row
+    ok.launch()
+    assert M.sync_status() == M.MORPH_OK
+    for j in jobs:
+        ref = oracle.apply(j["op"], img, 3, 3)
+        assert np.array_equal(unpack_words(j["dst"].words, W), ref)

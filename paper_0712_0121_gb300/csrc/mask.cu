@@ -61,28 +61,44 @@ __device__ __forceinline__ void lvl_ext4(const MaskArgs &a, int m, int r, int k,
 
 // Level m from level m - 1: A_2s(p) = A_s(p) op A_s(p + s), s = 2^(m-1),
 // for the row's words and its left pad.
+// A CTA of 256 threads covers rpb = max(1, 256 / width) rows of `width`
+// units (one unit per thread; wider rows loop); CTAs step over row blocks.
+struct RowTiling {
+    int width, rpb, ry, u0;
+    __device__ RowTiling(int w) : width(w) {
+        rpb = w <= (int)blockDim.x ? (int)blockDim.x / w : 1;
+        ry = w <= (int)blockDim.x ? (int)threadIdx.x / w : 0;
+        u0 = w <= (int)blockDim.x ? (int)threadIdx.x - ry * w : (int)threadIdx.x;
+    }
+    __device__ int ustep() const { return width <= (int)blockDim.x ? width : (int)blockDim.x; }
+};
+
+// Level m from level m - 1: A_2s(p) = A_s(p) op A_s(p + s), s = 2^(m-1),
+// for the row's words and its left pad.
 __global__ void __launch_bounds__(256) k_mask_level(const __grid_constant__ MaskArgs a, int m) {
     const int pad = mask_pad_words(a.nlev), lw = a.nw_valid + pad;
-    const int64_t n = (int64_t)a.H * lw;
     const int s = 1 << (m - 1);
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(i / lw), k = (int)(i - (int64_t)r * lw) - pad;
-        const uint32_t x = lvl_word(a, m - 1, r, k), y = lvl_ext(a, m - 1, r, k, s);
-        a.levels[lvl_index(a, m, r, k)] = a.use_or ? (x | y) : (x & y);
-    }
+    const RowTiling t(lw);
+    if (t.ry >= t.rpb) return;
+    for (int r = blockIdx.x * t.rpb + t.ry; r < a.H; r += gridDim.x * t.rpb)
+        for (int kk = t.u0; kk < lw; kk += t.ustep()) {
+            const int k = kk - pad;
+            const uint32_t x = lvl_word(a, m - 1, r, k), y = lvl_ext(a, m - 1, r, k, s);
+            a.levels[lvl_index(a, m, r, k)] = a.use_or ? (x | y) : (x & y);
+        }
 }
 
 // Output words [MW g, MW g + MW) of row y: op over the runs; words past the
 // row's pixels are written 0.
 __global__ void __launch_bounds__(256) k_mask_acc(const __grid_constant__ MaskArgs a) {
     const int ng = (a.nw_cover + MW - 1) / MW;
-    const int64_t n = (int64_t)a.H * ng;
     const bool use_or = a.use_or != 0;
     const uint32_t idv = use_or ? 0u : ONES, done = use_or ? ONES : 0u;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int y = (int)(i / ng), k0 = (int)(i - (int64_t)y * ng) * MW;
+    const RowTiling tl(ng);
+    if (tl.ry >= tl.rpb) return;
+    for (int y = blockIdx.x * tl.rpb + tl.ry; y < a.H; y += gridDim.x * tl.rpb)
+    for (int g = tl.u0; g < ng; g += tl.ustep()) {
+        const int k0 = g * MW;
         uint32_t acc[MW];
 #pragma unroll
         for (int t = 0; t < MW; ++t) acc[t] = idv;
@@ -112,9 +128,11 @@ __global__ void __launch_bounds__(256) k_mask_acc(const __grid_constant__ MaskAr
     }
 }
 
-int grid_for(int64_t n) {
-    int64_t b = (n + 255) / 256;
-    if (b > 152 * 8) b = 152 * 8;
+// CTAs of 256 threads for rows of `width` units (see RowTiling)
+int grid_rows(int width, int H) {
+    const int rpb = width <= 256 ? 256 / width : 1;
+    int64_t b = (H + rpb - 1) / rpb;
+    if (b > 152 * 16) b = 152 * 16;
     return b < 1 ? 1 : (int)b;
 }
 
@@ -126,11 +144,11 @@ size_t mask_levels_bytes(int W, int H, int nlev) {
 
 cudaError_t launch_mask_stage(const MaskArgs &a, cudaStream_t s) {
     for (int m = 1; m <= a.nlev; ++m) {
-        k_mask_level<<<grid_for((int64_t)a.H * (a.nw_valid + mask_pad_words(a.nlev))), 256, 0, s>>>(a, m);
+        k_mask_level<<<grid_rows(a.nw_valid + mask_pad_words(a.nlev), a.H), 256, 0, s>>>(a, m);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    k_mask_acc<<<grid_for((int64_t)a.H * ((a.nw_cover + MW - 1) / MW)), 256, 0, s>>>(a);
+    k_mask_acc<<<grid_rows((a.nw_cover + MW - 1) / MW, a.H), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

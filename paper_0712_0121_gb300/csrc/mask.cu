@@ -88,6 +88,49 @@ __global__ void __launch_bounds__(256) k_mask_level(const __grid_constant__ Mask
         }
 }
 
+// All levels of a block of rows in one launch: each row's level m-1 stays in
+// shared memory (two buffers per row, ping-pong) while level m is computed
+// from it and written out.  A row buffer holds the row's words, its left pad
+// and MASK_RPAD words of the identity on the right (the farthest a level
+// reaches: 2^(nlev-1) <= 2048 pixels).  Used while the buffers fit.
+constexpr int MASK_RPAD = 66;
+
+__global__ void __launch_bounds__(256) k_mask_levels(const __grid_constant__ MaskArgs a) {
+    extern __shared__ uint32_t lsm[];
+    const int pad = mask_pad_words(a.nlev), lw = a.nw_valid + pad, bw = lw + MASK_RPAD;
+    const uint32_t idv = a.use_or ? 0u : ONES;
+    const RowTiling t(lw);
+    const bool act = t.ry < t.rpb;
+    uint32_t *b0 = lsm + (size_t)(act ? t.ry : 0) * 2 * bw, *b1 = b0 + bw;
+    for (int rb = blockIdx.x * t.rpb; rb < a.H; rb += gridDim.x * t.rpb) {
+        const int r = rb + t.ry;
+        const bool live = act && r < a.H;
+        if (live)
+            for (int u = t.u0; u < bw; u += t.ustep()) {
+                const int k = u - pad;
+                b0[u] = k < a.nw_valid ? lvl_word(a, 0, r, k) : idv;  // k < 0: identity
+                b1[u] = idv;
+            }
+        __syncthreads();
+        uint32_t *cur = b0, *nxt = b1;
+        for (int m = 1; m <= a.nlev; ++m) {
+            const int s = 1 << (m - 1), q = s >> 5, sh = s & 31;
+            if (live)
+                for (int u = t.u0; u < lw; u += t.ustep()) {
+                    const uint32_t x = cur[u], lo = cur[u + q];
+                    const uint32_t y = sh ? __funnelshift_r(lo, cur[u + q + 1], sh) : lo;
+                    const uint32_t v = a.use_or ? (x | y) : (x & y);
+                    nxt[u] = v;
+                    a.levels[lvl_index(a, m, r, u - pad)] = v;
+                }
+            __syncthreads();
+            uint32_t *tmp = cur;
+            cur = nxt;
+            nxt = tmp;
+        }
+    }
+}
+
 // Output words [MW g, MW g + MW) of row y: op over the runs; words past the
 // row's pixels are written 0.
 __global__ void __launch_bounds__(256) k_mask_acc(const __grid_constant__ MaskArgs a) {
@@ -143,7 +186,15 @@ size_t mask_levels_bytes(int W, int H, int nlev) {
 }
 
 cudaError_t launch_mask_stage(const MaskArgs &a, cudaStream_t s) {
-    for (int m = 1; m <= a.nlev; ++m) {
+    const int lw = a.nw_valid + mask_pad_words(a.nlev);
+    const int rpb = lw <= 256 ? 256 / lw : 1;
+    const size_t lsmem = (size_t)rpb * 2 * (lw + MASK_RPAD) * sizeof(uint32_t);
+    if (a.nlev > 0 && lsmem <= 48 * 1024) {
+        k_mask_levels<<<grid_rows(lw, a.H), 256, lsmem, s>>>(a);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    for (int m = 1; m <= a.nlev && !(lsmem <= 48 * 1024); ++m) {
         k_mask_level<<<grid_rows(a.nw_valid + mask_pad_words(a.nlev), a.H), 256, 0, s>>>(a, m);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -3,14 +3,15 @@
 //
 // The host builds a plan: a job table and a list of work items.  A packed
 // job is one phase of independent tiles (the fused tile of packed_tile.cuh).
-// An RLE job is a chain of phases — bitmap->RLE count, scan, write; per
-// erosion stage the run pass (count, scan, write) or the between-line pass
-// (rows to a bitmap, run counts of the rows, scan, encode; the last stage's
-// rows go straight to the job's packed output); RLE->bitmap after a run-pass stage —
-// whose items depend on every item of the job's previous phase.
-// Items are listed by level (a job's phase index, shifted past the phases of
-// the job it depends on) and claimed in list order from a device queue by
-// persistent CTAs.  An item waits (bounded spin with acquire loads) only
+// An RLE job is a chain of phases — bitmap->RLE count, scan, write (shared:
+// RLE jobs on the same source page read one job's encode); per erosion stage
+// the run pass (count, scan, write) or the between-line pass (rows to a
+// bitmap; for a first stage of two, its run counts, scan and encode; the
+// last stage's rows go straight to the job's packed output); RLE->bitmap
+// after a run-pass stage — whose items depend on every item of the job's
+// previous phase.  Items are listed by level (a job's phase index, shifted
+// past the phase of the job it depends on) and claimed in list order from a
+// device queue by persistent CTAs.  An item waits (bounded spin with acquire loads) only
 // for items of smaller index, which running CTAs have already claimed, so
 // the launch cannot deadlock; a wait that exceeds the time limit latches
 // MORPH_ETIMEOUT and makes every CTA stop.

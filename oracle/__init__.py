@@ -1,4 +1,5 @@
-"""Plain CPU oracle for rectangular binary morphology and run-length coding.
+"""Plain CPU oracle for rectangular binary morphology, run-length coding,
+connected components of RLE images and run-length statistics.
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
@@ -72,6 +73,13 @@ def _load():
             lib.oracle_rle_encode.restype = None
             lib.oracle_rle_decode.argtypes = [u8p, i32p, u16p, ci, ci]
             lib.oracle_rle_decode.restype = ci
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            lib.oracle_rle_components.argtypes = [i32p, i32p, u16p, ci, ci]
+            lib.oracle_rle_components.restype = ctypes.c_int64
+            lib.oracle_rle_component_stats.argtypes = [i64p, i32p, i32p, u16p, ci, ctypes.c_int64]
+            lib.oracle_rle_component_stats.restype = None
+            lib.oracle_run_length_hist.argtypes = [i64p, i64p, i32p, u16p, ci, ci]
+            lib.oracle_run_length_hist.restype = None
             _lib = lib
     return _lib
 
@@ -325,3 +333,55 @@ def rle_apply(op: str, row_ptr, runs, W, H, sw, sh, ox=None, oy=None, mode="brut
     byte-image op, encode the result."""
     img = rle_decode(row_ptr, runs, W, H)
     return rle_encode(apply(op, img, sw, sh, ox, oy, mode, threads))
+
+
+# ------------------------------------------------- connected components ---
+
+def _rle_arrays(row_ptr, runs):
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ru = np.ascontiguousarray(runs, dtype=np.uint16).reshape(-1, 2)
+    if ru.shape[0] == 0:
+        ru = np.zeros((1, 2), np.uint16)  # a valid pointer; no run is read
+    return rp, ru
+
+
+def rle_components(row_ptr, runs, H: int, connectivity: int = 4):
+    """Label the runs of an RLE image by connected component (union-find over
+    runs that touch in adjacent lines, section "Connected Component Extraction
+    and Statistics").  Returns ``(labels int32[N], n_components)``; components
+    are numbered in raster order of their first run.  connectivity 4: runs
+    sharing a column; 8: also diagonal neighbours."""
+    if connectivity not in (4, 8):
+        raise ValueError("connectivity must be 4 or 8")
+    rp, ru = _rle_arrays(row_ptr, runs)
+    n = int(rp[H])
+    labels = np.zeros(max(n, 1), np.int32)
+    count = _load().oracle_rle_components(_ptr(labels, ctypes.c_int32), _ptr(rp, ctypes.c_int32),
+                                          _ptr(ru, ctypes.c_uint16), int(H), int(connectivity))
+    return labels[:n], int(count)
+
+
+def rle_component_stats(labels, n_components: int, row_ptr, runs, H: int) -> np.ndarray:
+    """Per component: ``int64[n, 7]`` = x0, y0, x1, y1 (half-open bounding
+    box), area, sum of x, sum of y over its pixels (pixel-by-pixel loop)."""
+    rp, ru = _rle_arrays(row_ptr, runs)
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    if lab.size == 0:
+        lab = np.zeros(1, np.int32)
+    out = np.zeros((max(n_components, 1), 7), np.int64)
+    _load().oracle_rle_component_stats(_ptr(out, ctypes.c_int64), _ptr(lab, ctypes.c_int32),
+                                       _ptr(rp, ctypes.c_int32), _ptr(ru, ctypes.c_uint16), int(H),
+                                       int(n_components))
+    return out[:n_components]
+
+
+def run_length_hist(row_ptr, runs, W: int, H: int):
+    """Histograms ``(black int64[W+1], white int64[W+1])`` of the lengths of
+    the black runs and of the white runs (gaps, those at the row ends
+    included; an empty row is one white run of length W)."""
+    rp, ru = _rle_arrays(row_ptr, runs)
+    black = np.zeros(W + 1, np.int64)
+    white = np.zeros(W + 1, np.int64)
+    _load().oracle_run_length_hist(_ptr(black, ctypes.c_int64), _ptr(white, ctypes.c_int64),
+                                   _ptr(rp, ctypes.c_int32), _ptr(ru, ctypes.c_uint16), int(W), int(H))
+    return black, white

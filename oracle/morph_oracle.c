@@ -1,5 +1,6 @@
 /*
- * Plain CPU oracle for rectangular binary morphology and run-length coding.
+ * Plain CPU oracle for rectangular binary morphology, run-length coding,
+ * connected components of RLE images and run-length statistics.
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call this code:
  * only tests/, the smoke check in __graft_entry__ and the cpu_baseline leg of
@@ -310,4 +311,117 @@ EXPORT int oracle_rle_decode(uint8_t *out, const int32_t *row_ptr,
         }
     }
     return 0;
+}
+
+/* ------------------------------------------------- connected components */
+
+/* Section "Connected Component Extraction and Statistics": every run of
+ * the RLE image gets a label, each label starts as its own set of a
+ * union-find structure, and the lines are visited top to bottom merging
+ * every run of the current line with each run of the line above that it
+ * touches.  Finally each run is relabelled by its set's representative.
+ *
+ * Touching (the paper: the runs' intervals overlap, which is the line
+ * adjacency graph of section "Other Operations"):
+ *   conn == 4: [s, e) and [s', e') share a column: s < e' and s' < e;
+ *   conn == 8: they also touch diagonally:         s <= e' and s' <= e.
+ * Canonical numbering (the paper leaves the representative open): the
+ * components are numbered 0, 1, ... in the order in which their first run
+ * appears in raster order (row by row, left to right), so the labels are
+ * unique.  Returns the number of components. */
+static int32_t uf_find(int32_t *parent, int32_t x) {
+    int32_t r = x;
+    while (parent[r] != r) r = parent[r];
+    while (parent[x] != r) {  /* path compression */
+        int32_t n = parent[x];
+        parent[x] = r;
+        x = n;
+    }
+    return r;
+}
+
+static void uf_union(int32_t *parent, int32_t a, int32_t b) {
+    a = uf_find(parent, a);
+    b = uf_find(parent, b);
+    if (a != b) parent[a > b ? a : b] = a < b ? a : b;
+}
+
+EXPORT int64_t oracle_rle_components(int32_t *label, const int32_t *row_ptr,
+                                     const uint16_t *runs, int H, int conn) {
+    const int32_t n = row_ptr[H];
+    const int d = conn == 8 ? 1 : 0;
+    int32_t *parent = (int32_t *)malloc(sizeof(int32_t) * (n > 0 ? n : 1));
+    int32_t *number = (int32_t *)malloc(sizeof(int32_t) * (n > 0 ? n : 1));
+    for (int32_t i = 0; i < n; i++) parent[i] = i;
+    for (int y = 1; y < H; y++) {
+        /* the runs of both lines are ascending: one linear walk */
+        int32_t a = row_ptr[y - 1];
+        const int32_t a_end = row_ptr[y];
+        for (int32_t k = row_ptr[y]; k < row_ptr[y + 1]; k++) {
+            const int s = runs[2 * k], e = runs[2 * k + 1];
+            /* runs above that end before this one starts can touch no later run */
+            while (a < a_end && runs[2 * a + 1] + d <= s) a++;
+            for (int32_t b = a; b < a_end && runs[2 * b] < e + d; b++)
+                uf_union(parent, k, b);
+        }
+    }
+    int64_t count = 0;
+    for (int32_t i = 0; i < n; i++) number[i] = -1;
+    for (int32_t i = 0; i < n; i++) {
+        const int32_t r = uf_find(parent, i);
+        if (number[r] < 0) number[r] = (int32_t)count++;
+        label[i] = number[r];
+    }
+    free(parent);
+    free(number);
+    return count;
+}
+
+/* Statistics over the labelled runs (same section: iterate through the runs
+ * and accumulate into arrays indexed by the label).  Per component c,
+ * stats[7 c + .]: x0, y0, x1, y1 (bounding box, half-open), area (pixels),
+ * sum of x, sum of y over its pixels.  Pixel by pixel on purpose. */
+EXPORT void oracle_rle_component_stats(int64_t *stats, const int32_t *label,
+                                       const int32_t *row_ptr, const uint16_t *runs,
+                                       int H, int64_t ncomp) {
+    for (int64_t c = 0; c < ncomp; c++) {
+        int64_t *t = stats + 7 * c;
+        t[0] = INT64_MAX; t[1] = INT64_MAX; t[2] = INT64_MIN; t[3] = INT64_MIN;
+        t[4] = 0; t[5] = 0; t[6] = 0;
+    }
+    for (int y = 0; y < H; y++) {
+        for (int32_t k = row_ptr[y]; k < row_ptr[y + 1]; k++) {
+            int64_t *t = stats + 7 * (int64_t)label[k];
+            for (int x = runs[2 * k]; x < runs[2 * k + 1]; x++) {
+                if (x < t[0]) t[0] = x;
+                if (y < t[1]) t[1] = y;
+                if (x + 1 > t[2]) t[2] = x + 1;
+                if (y + 1 > t[3]) t[3] = y + 1;
+                t[4] += 1;
+                t[5] += x;
+                t[6] += y;
+            }
+        }
+    }
+}
+
+/* Run-length statistics (section "Other Operations"): histograms of the
+ * lengths of the black runs (1-pixels) and of the white runs (maximal gaps
+ * of 0-pixels in a row, including those at the row's ends; an empty row is
+ * one white run of length W), read off the runs of each line.  black[L] and
+ * white[L], L = 0..W, count the runs of length L. */
+EXPORT void oracle_run_length_hist(int64_t *black, int64_t *white, const int32_t *row_ptr,
+                                   const uint16_t *runs, int W, int H) {
+    memset(black, 0, sizeof(int64_t) * (W + 1));
+    memset(white, 0, sizeof(int64_t) * (W + 1));
+    for (int y = 0; y < H; y++) {
+        int prev_end = 0;
+        for (int32_t k = row_ptr[y]; k < row_ptr[y + 1]; k++) {
+            const int s = runs[2 * k], e = runs[2 * k + 1];
+            black[e - s]++;
+            if (s > prev_end) white[s - prev_end]++;
+            prev_end = e;
+        }
+        if (W > prev_end) white[W - prev_end]++;
+    }
 }

@@ -364,6 +364,8 @@ def run_probe(args):
     except (OSError, KeyError, ValueError):
         pass
     results = []
+    if args.probe == "cc":
+        return run_probe_cc(args, M, src, Wt, Ht, peak, stream)
     for se in args.probe_se.split(","):
         if args.probe == "mask":
             # "d<r>": digital disc of radius r; "WxH": the full rectangle as a mask
@@ -410,6 +412,51 @@ def run_probe(args):
             raise SystemExit(1)
     print(json.dumps({"probe": args.probe, "op": args.probe_op, "width": Wt, "height": Ht,
                       "peak_gb_s": peak, "results": results}))
+
+
+def run_probe_cc(args, M, src, Wt, Ht, peak, stream):
+    """Connected components (connectivity 4 or 8, with statistics) and the
+    run-length histograms of the RLE form of the stack; --probe-se lists
+    "4", "8" and "hist".  Algorithmic bytes: the runs and row offsets read
+    once, one label written per run and one record per component."""
+    import torch
+    cap = Ht * args.rle_runs_per_row
+    rle = M.Rle.empty(Wt, Ht, cap)
+    M.rle_from_bitmap(rle, src)
+    n_runs = int(rle.n_runs.item())
+    labels = torch.empty(max(n_runs, 1), dtype=torch.int32, device="cuda")
+    ws = torch.empty(M.components_workspace_size(rle), dtype=torch.uint8, device="cuda")
+    nc = torch.zeros(1, dtype=torch.int64, device="cuda")
+    base = 4 * n_runs + 4 * (Ht + 1)
+    results = []
+    for tok in args.probe_se.split(","):
+        if tok == "hist":
+            black = torch.empty(Wt + 1, dtype=torch.int64, device="cuda")
+            white = torch.empty(Wt + 1, dtype=torch.int64, device="cuda")
+            fn = lambda: M.run_length_hist(rle, black, white)  # noqa: E731
+            alg, extra = base, {}
+        else:
+            conn = int(tok)
+            M.rle_components(rle, conn, labels=labels, stats=False, n_components=nc, workspace=ws)
+            n = int(nc.item())
+            stats = torch.empty((max(n, 1), 7), dtype=torch.int64, device="cuda")
+            fn = lambda: M.rle_components(rle, conn, labels=labels, stats=stats,  # noqa: E731
+                                          n_components=nc, workspace=ws)
+            alg, extra = base + 4 * n_runs + 56 * n, {"components": n}
+        fn()
+        torch.cuda.synchronize()
+        ms = statistics.median(time_launches(fn, args.probe_reps, stream))
+        st = M.sync_status()
+        r = {"se": tok, "ms": round(ms, 4), "gpix_s": round(Wt * Ht / ms / 1e6, 1),
+             "gruns_s": round(n_runs / ms / 1e6, 2), "alg_gb_s": round(alg / ms / 1e6, 1),
+             "frac": round(alg / ms / 1e6 / peak, 3), "status": st}
+        r.update(extra)
+        results.append(r)
+        if st != M.MORPH_OK:
+            print(json.dumps(r))
+            raise SystemExit(1)
+    print(json.dumps({"probe": "cc", "width": Wt, "height": Ht, "runs": n_runs, "peak_gb_s": peak,
+                      "results": results}))
 
 
 def run_ours(args):
@@ -617,7 +664,7 @@ def main():
     ap.add_argument("--batch-pages", type=int, default=256)
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--tune-cache", default=os.path.join("/tmp", "morph_tune_cache.json"))
-    ap.add_argument("--probe", choices=["packed", "rle", "mask"], default=None,
+    ap.add_argument("--probe", choices=["packed", "rle", "mask", "cc"], default=None,
                     help="run one standalone op on a tall page stack (ncu target) and exit")
     ap.add_argument("--probe-op", default="erode")
     ap.add_argument("--probe-se", default="3x3")

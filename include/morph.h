@@ -217,6 +217,53 @@ MORPH_API morph_status rle_from_bitmap(const morph_image *dst_rle, const morph_i
 MORPH_API morph_status rle_to_bitmap(const morph_image *dst_packed, const morph_image *src_rle,
                            void *stream);
 
+/* ------------------------------------------------ connected components --
+ * Section "Connected Component Extraction and Statistics".
+ * morph_rle_components labels every run of an RLE image by its connected
+ * component: each run starts as its own set of a union-find structure, every
+ * run is merged with the runs of the line above that it touches, and each
+ * run is then relabelled by its set.
+ *   connectivity 4: runs in adjacent lines touch when they share a column
+ *                   ([s, e) and [s', e'): s < e' and s' < e);
+ *                8: also when they meet at a corner (s <= e' and s' <= e).
+ *   labels (device int32[src->capacity_runs]): labels[k] for the image's
+ *     runs k = 0 .. n_runs-1 in row order; components are numbered 0, 1, ...
+ *     in the raster order of their first run, so the labelling is unique.
+ *   n_components (device int64, required): the number of components.
+ *   stats (device, may be NULL): for component c < max_components,
+ *     stats[c] = {x0, y0, x1, y1 (half-open bounding box), area (pixels),
+ *     sum_x, sum_y (sums over its pixels; centroid = sum / area)}.
+ *     If there are more than max_components components MORPH_ECAPACITY is
+ *     latched (see morph_sync_status), labels and n_components are still
+ *     complete and stats holds the first max_components.
+ * The src RLE must be canonical (every producer here writes it so).
+ * Workspace (device, 256-byte aligned): morph_components_workspace_size()
+ * bytes.  Errors: MORPH_EINVAL (arguments, non-RLE src, NULL labels or
+ * n_components, connectivity not 4 or 8, overlapping buffers), MORPH_ENOMEM
+ * (workspace too small), MORPH_ECUDA. */
+typedef struct morph_component {
+    int64_t x0, y0, x1, y1;  /* bounding box [x0, x1) x [y0, y1) */
+    int64_t area;            /* pixels */
+    int64_t sum_x, sum_y;    /* sums of the pixels' coordinates */
+} morph_component;
+
+MORPH_API size_t morph_components_workspace_size(const morph_image *src_rle);
+MORPH_API morph_status morph_rle_components(int32_t *labels, morph_component *stats,
+                                            int64_t max_components, int64_t *n_components,
+                                            const morph_image *src_rle, int connectivity,
+                                            void *workspace, size_t workspace_bytes,
+                                            void *stream);
+
+/* Run-length statistics (section "Other Operations"): histograms of the
+ * lengths of the black runs (1-pixels) and of the white runs (maximal gaps
+ * of 0-pixels in a row, the ones at either end of the row included; an empty
+ * row is one white run of length width) of an RLE image.  black_hist and
+ * white_hist: device int64[width + 1], overwritten; entry L counts the runs
+ * of length L (entry 0 stays 0).  Either may be NULL.  No workspace.
+ * Errors: MORPH_EINVAL, MORPH_ECUDA. */
+MORPH_API morph_status morph_run_length_hist(int64_t *black_hist, int64_t *white_hist,
+                                             const morph_image *src_rle, void *stream);
+
 /* ----------------------------------------------------------------- batch --
  * Many uneven pages, each with its own op, rectangle and path, in ONE
  * persistent kernel launch.  A job reads a packed src page and writes a

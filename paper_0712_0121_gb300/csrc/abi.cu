@@ -535,6 +535,81 @@ morph_status rle_to_bitmap(const morph_image *dst_packed, const morph_image *src
     return MORPH_OK;
 }
 
+size_t morph_components_workspace_size(const morph_image *src_rle) {
+    if (!src_rle || src_rle->fmt != MORPH_RLE || src_rle->height < 1 || src_rle->capacity_runs < 0 ||
+        src_rle->capacity_runs > INT32_MAX)
+        return 0;
+    const size_t H = (size_t)src_rle->height;
+    const size_t cap = src_rle->capacity_runs > 0 ? (size_t)src_rle->capacity_runs : 1;
+    return align256(H * 4) + align256((H + 1) * 4) + align256(cap * 4);
+}
+
+morph_status morph_rle_components(int32_t *labels, morph_component *stats, int64_t max_components,
+                                  int64_t *n_components, const morph_image *src_rle,
+                                  int connectivity, void *workspace, size_t workspace_bytes,
+                                  void *stream) {
+    morph_status st = check_image(src_rle, "src");
+    if (st) return st;
+    if (src_rle->fmt != MORPH_RLE) return fail(MORPH_EINVAL, "morph_rle_components needs an RLE src");
+    if (src_rle->capacity_runs > INT32_MAX)
+        return fail(MORPH_EINVAL, "src.capacity_runs above 2^31 - 1 (int32 labels)");
+    if (connectivity != 4 && connectivity != 8)
+        return fail(MORPH_EINVAL, "connectivity %d is neither 4 nor 8", connectivity);
+    if (!labels || !n_components) return fail(MORPH_EINVAL, "labels and n_components must not be NULL");
+    if ((uintptr_t)labels % 4 || (uintptr_t)n_components % 8 || (uintptr_t)stats % 8)
+        return fail(MORPH_EINVAL, "labels, n_components or stats misaligned");
+    if (stats && max_components < 0) return fail(MORPH_EINVAL, "max_components < 0");
+    const int H = src_rle->height;
+    const int64_t cap = src_rle->capacity_runs;
+    const Range srp{(uintptr_t)src_rle->row_ptr, (uintptr_t)(src_rle->row_ptr + H + 1)};
+    const Range sru{(uintptr_t)src_rle->runs, (uintptr_t)(src_rle->runs + 2 * cap)};
+    const Range lr{(uintptr_t)labels, (uintptr_t)(labels + cap)};
+    const Range sr{(uintptr_t)stats, (uintptr_t)(stats ? stats + max_components : stats)};
+    const Range nr{(uintptr_t)n_components, (uintptr_t)(n_components + 1)};
+    if (overlap(lr, srp) || overlap(lr, sru) || overlap(sr, srp) || overlap(sr, sru) ||
+        overlap(lr, sr) || overlap(nr, lr) || overlap(nr, sr) || overlap(nr, srp) || overlap(nr, sru))
+        return fail(MORPH_EINVAL, "labels, stats, n_components and src overlap");
+    const size_t need = morph_components_workspace_size(src_rle);
+    if (!workspace || workspace_bytes < need)
+        return fail(MORPH_ENOMEM, "the components need %zu bytes of workspace, got %zu", need,
+                    workspace ? workspace_bytes : (size_t)0);
+    if ((uintptr_t)workspace % 256) return fail(MORPH_EINVAL, "workspace is not 256-byte aligned");
+    char *w = (char *)workspace;
+    MorphCC c;
+    c.labels = labels;
+    c.stats = stats;
+    c.max_components = stats ? max_components : 0;
+    c.n_components = n_components;
+    c.counts = (int32_t *)w;
+    c.rootptr = (int32_t *)(w + align256((size_t)H * 4));
+    c.rank = (int32_t *)(w + align256((size_t)H * 4) + align256((size_t)(H + 1) * 4));
+    cudaError_t e = launch_rle_components(rle_in(src_rle), connectivity, c, device_status_ptr(),
+                                          (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "connected components launch");
+    return MORPH_OK;
+}
+
+morph_status morph_run_length_hist(int64_t *black_hist, int64_t *white_hist,
+                                   const morph_image *src_rle, void *stream) {
+    morph_status st = check_image(src_rle, "src");
+    if (st) return st;
+    if (src_rle->fmt != MORPH_RLE) return fail(MORPH_EINVAL, "morph_run_length_hist needs an RLE src");
+    if ((uintptr_t)black_hist % 8 || (uintptr_t)white_hist % 8)
+        return fail(MORPH_EINVAL, "histograms are not 8-byte aligned");
+    const int W = src_rle->width, H = src_rle->height;
+    const int64_t cap = src_rle->capacity_runs;
+    const Range srp{(uintptr_t)src_rle->row_ptr, (uintptr_t)(src_rle->row_ptr + H + 1)};
+    const Range sru{(uintptr_t)src_rle->runs, (uintptr_t)(src_rle->runs + 2 * cap)};
+    const Range br{(uintptr_t)black_hist, (uintptr_t)(black_hist ? black_hist + W + 1 : black_hist)};
+    const Range wr{(uintptr_t)white_hist, (uintptr_t)(white_hist ? white_hist + W + 1 : white_hist)};
+    if (overlap(br, wr) || overlap(br, srp) || overlap(br, sru) || overlap(wr, srp) || overlap(wr, sru))
+        return fail(MORPH_EINVAL, "histograms and src overlap");
+    if (!black_hist && !white_hist) return MORPH_OK;
+    cudaError_t e = launch_run_length_hist(rle_in(src_rle), black_hist, white_hist, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "run-length histogram launch");
+    return MORPH_OK;
+}
+
 morph_status morph_sync_status(void *stream) {
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");

@@ -155,6 +155,24 @@ int vpass_kmax(int sh);  // counter width for a window of sh rows
 // rows handled by one work item of the row-wise RLE kernels
 constexpr int RLE_ROWS_PER_ITEM = 64;
 
+// Exclusive prefix sum of counts[0..H) into row_ptr[0..H] (row_ptr[H] =
+// total, also stored to *n_runs when not NULL); a total above capacity
+// latches MORPH_ECAPACITY.  One launch up to 8192 entries, three above.
+void launch_scan_rows(const int32_t *counts, int H, int32_t *row_ptr, int64_t *n_runs,
+                      int64_t capacity, int *status, cudaStream_t s);
+
+// Connected components of an RLE image (cc.cu).  labels: int32[runs];
+// counts: int32[H], rootptr: int32[H+1], rank: int32[runs] scratch.
+struct MorphCC {
+    int32_t *labels;
+    morph_component *stats;
+    int64_t max_components;
+    int64_t *n_components;
+    int32_t *counts, *rootptr, *rank;
+};
+cudaError_t launch_rle_components(RleIn in, int conn, MorphCC c, int *status, cudaStream_t s);
+cudaError_t launch_run_length_hist(RleIn in, int64_t *black, int64_t *white, cudaStream_t s);
+
 cudaError_t launch_rle_from_bitmap(const uint32_t *src, int64_t sstride, int W, int H,
                                    RleOut out, int32_t *counts, int *status, cudaStream_t s);
 cudaError_t launch_rle_to_bitmap(RleIn in, uint32_t *dst, int64_t dstride, int nw_cover,

@@ -112,18 +112,6 @@ int row_items(int H) {
     return n < 1 ? 1 : n;
 }
 
-// counts[0..H) -> row_ptr[0..H], *n_runs, capacity check (see scan_rows_block)
-void launch_scan_rows(const int32_t *counts, int H, int32_t *row_ptr, int64_t *n_runs,
-                      int64_t capacity, int *status, cudaStream_t s) {
-    if (H <= 2 * SCAN_SEG) {
-        k_scan_rows<<<1, 1024, 0, s>>>(counts, H, row_ptr, n_runs, capacity, status);
-        return;
-    }
-    const int nseg = (H + SCAN_SEG - 1) / SCAN_SEG;
-    k_scan_seg_sums<<<nseg, 1024, 0, s>>>(counts, H, row_ptr);
-    k_scan_seg_tops<<<1, 1024, 0, s>>>(H, nseg, row_ptr, n_runs, capacity, status);
-    k_scan_seg_rows<<<nseg, 1024, 0, s>>>(counts, H, row_ptr);
-}
 
 template <int NWT, int KMAX>
 cudaError_t launch_vt(const VArgs &a, cudaStream_t s) {
@@ -169,6 +157,19 @@ cudaError_t launch_vk(const VArgs &a, cudaStream_t s) {
 }
 
 }  // namespace
+
+// counts[0..H) -> row_ptr[0..H], *n_runs, capacity check (see scan_rows_block)
+void launch_scan_rows(const int32_t *counts, int H, int32_t *row_ptr, int64_t *n_runs,
+                      int64_t capacity, int *status, cudaStream_t s) {
+    if (H <= 2 * SCAN_SEG) {
+        k_scan_rows<<<1, 1024, 0, s>>>(counts, H, row_ptr, n_runs, capacity, status);
+        return;
+    }
+    const int nseg = (H + SCAN_SEG - 1) / SCAN_SEG;
+    k_scan_seg_sums<<<nseg, 1024, 0, s>>>(counts, H, row_ptr);
+    k_scan_seg_tops<<<1, 1024, 0, s>>>(H, nseg, row_ptr, n_runs, capacity, status);
+    k_scan_seg_rows<<<nseg, 1024, 0, s>>>(counts, H, row_ptr);
+}
 
 int vpass_kmax(int sh) {
     const int K = bit_length(sh);

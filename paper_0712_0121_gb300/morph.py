@@ -92,6 +92,12 @@ def _load():
     lib.rle_from_bitmap.restype = ci
     lib.rle_to_bitmap.argtypes = [img_p, img_p, vp]
     lib.rle_to_bitmap.restype = ci
+    lib.morph_components_workspace_size.argtypes = [img_p]
+    lib.morph_components_workspace_size.restype = sz
+    lib.morph_rle_components.argtypes = [vp, vp, ctypes.c_int64, vp, img_p, ci, vp, sz, vp]
+    lib.morph_rle_components.restype = ci
+    lib.morph_run_length_hist.argtypes = [vp, vp, img_p, vp]
+    lib.morph_run_length_hist.restype = ci
     lib.morph_sync_status.argtypes = [vp]
     lib.morph_sync_status.restype = ci
     lib.morph_last_error.argtypes = []
@@ -359,6 +365,58 @@ def rle_from_bitmap(dst: Rle, src: Packed, workspace: torch.Tensor | None = None
 def rle_to_bitmap(dst: Packed, src: Rle, stream=None) -> None:
     _check(_lib.rle_to_bitmap(ctypes.byref(dst.desc()), ctypes.byref(src.desc()),
                               _stream_handle(stream)))
+
+
+# ------------------------------------------------- connected components
+
+COMPONENT_FIELDS = ("x0", "y0", "x1", "y1", "area", "sum_x", "sum_y")
+
+
+def components_workspace_size(src: Rle) -> int:
+    return int(_lib.morph_components_workspace_size(ctypes.byref(src.desc())))
+
+
+def rle_components(src: Rle, connectivity: int = 4, labels: torch.Tensor | None = None,
+                   stats: torch.Tensor | bool | None = True, n_components: torch.Tensor | None = None,
+                   workspace: torch.Tensor | None = None, stream=None):
+    """Connected components of an RLE image (union-find over runs that touch
+    in adjacent lines).  Returns ``(labels, stats, n_components)`` as device
+    tensors: ``labels`` int32[capacity] (one per run, components numbered in
+    raster order of their first run), ``stats`` int64[max_components, 7]
+    with the columns of ``COMPONENT_FIELDS`` (or None), ``n_components``
+    int64[1].  ``stats=True`` sizes the statistics for every possible
+    component (one per run); pass a tensor to bound them."""
+    dev = src.row_ptr.device
+    if labels is None:
+        labels = torch.empty(max(src.capacity, 1), dtype=torch.int32, device=dev)
+    if stats is True:
+        stats = torch.empty((max(src.capacity, 1), 7), dtype=torch.int64, device=dev)
+    elif stats is False:
+        stats = None
+    if n_components is None:
+        n_components = torch.zeros(1, dtype=torch.int64, device=dev)
+    if workspace is None:
+        workspace = torch.empty(max(components_workspace_size(src), 1), dtype=torch.uint8, device=dev)
+    wp, wn = _ws_args(workspace)
+    max_c = int(stats.shape[0]) if stats is not None else 0
+    _check(_lib.morph_rle_components(labels.data_ptr(), stats.data_ptr() if stats is not None else None,
+                                     max_c, n_components.data_ptr(), ctypes.byref(src.desc()),
+                                     int(connectivity), wp, wn, _stream_handle(stream)))
+    return labels, stats, n_components
+
+
+def run_length_hist(src: Rle, black: torch.Tensor | None = None, white: torch.Tensor | None = None,
+                    stream=None):
+    """Histograms int64[width + 1] of black and white run lengths of an RLE
+    image (white runs: the gaps of each row, those at its ends included)."""
+    dev = src.row_ptr.device
+    if black is None:
+        black = torch.empty(src.width + 1, dtype=torch.int64, device=dev)
+    if white is None:
+        white = torch.empty(src.width + 1, dtype=torch.int64, device=dev)
+    _check(_lib.morph_run_length_hist(black.data_ptr(), white.data_ptr(), ctypes.byref(src.desc()),
+                                      _stream_handle(stream)))
+    return black, white
 
 
 def sync_status(stream=None) -> int:

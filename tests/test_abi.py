@@ -110,3 +110,43 @@ def test_packed_workspace_only_for_wide_rectangles(M):
     assert f(2, ctypes.byref(dst), ctypes.byref(src), 600, 1, 0, 0) > 0
     small = _img(M, W=100)
     assert f(0, ctypes.byref(_img(M, W=100, words=0x9000000)), ctypes.byref(small), 600, 1, 0, 0) == 0
+
+
+def test_components_and_histogram_checks(M):
+    """Host checks of the connected-component and run-length-statistics
+    entry points; every case fails before any device work."""
+    L = M.lib()
+
+    def rle(W=100, H=10, rp=0x1000, runs=0x2000, cap=100):
+        d = M.morph_image()
+        d.fmt, d.width, d.height = 2, W, H
+        d.row_ptr, d.runs, d.capacity_runs = rp, runs, cap
+        return d
+    src = rle()
+    need = L.morph_components_workspace_size(ctypes.byref(src))
+    assert need >= 4 * (10 + 11 + 100)
+    assert need % 256 == 0
+    lab, st, nc, ws = 0x10000, 0x20000, 0x30000, 0x40000
+
+    def cc(labels=lab, stats=st, max_c=50, n=nc, s=src, conn=4, w=ws, nw=need):
+        return L.morph_rle_components(labels, stats, max_c, n, ctypes.byref(s) if s else None, conn,
+                                      w, nw, None)
+    assert cc(conn=6) == M.MORPH_EINVAL
+    assert cc(labels=None) == M.MORPH_EINVAL
+    assert cc(n=None) == M.MORPH_EINVAL
+    assert cc(s=None) == M.MORPH_EINVAL
+    assert cc(s=_img(M, words=0x90000)) == M.MORPH_EINVAL       # packed src
+    assert cc(max_c=-1) == M.MORPH_EINVAL
+    assert cc(labels=0x1002) == M.MORPH_EINVAL                  # misaligned
+    assert cc(labels=0x2000 + 8) == M.MORPH_EINVAL              # labels overlap the runs
+    assert cc(stats=0x10000 + 64) == M.MORPH_EINVAL             # stats overlap the labels
+    assert cc(w=None) == M.MORPH_ENOMEM
+    assert cc(nw=need - 1) == M.MORPH_ENOMEM
+    assert cc(w=ws + 16) == M.MORPH_EINVAL                      # workspace not 256-aligned
+    packed = _img(M, words=0x90000)
+    assert L.morph_components_workspace_size(ctypes.byref(packed)) == 0
+    hb, hw = 0x50000, 0x60000
+    assert L.morph_run_length_hist(hb, hw, ctypes.byref(packed), None) == M.MORPH_EINVAL
+    assert L.morph_run_length_hist(hb, hb + 8, ctypes.byref(src), None) == M.MORPH_EINVAL  # overlap
+    assert L.morph_run_length_hist(hb + 4, hw, ctypes.byref(src), None) == M.MORPH_EINVAL  # misaligned
+    assert L.morph_run_length_hist(None, None, ctypes.byref(src), None) == M.MORPH_OK      # nothing to do

@@ -120,3 +120,18 @@ def test_run_length_hist_pages():
         b, w = M.run_length_hist(rle)
         assert np.array_equal(b.cpu().numpy(), b_ref)
         assert np.array_equal(w.cpu().numpy(), w_ref)
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+def test_crowded_lines(conn):
+    """Lines with more runs than a band keeps in shared memory (alternating
+    pixels: 4500 runs per line) and bands cut into several sub-bands (about
+    a thousand runs per line): the seams inside a band are joined in global
+    memory."""
+    H, W = 70, 9000
+    img = np.zeros((H, W), np.uint8)
+    img[:, ::2] = 1
+    noise = synth.random_bits((H, W), 31 + conn, 0.3)
+    img[10:40] |= noise[10:40]
+    check_components(img, conn)
+    check_components(synth.random_bits((200, 4000), 77 + conn, 0.5), conn)

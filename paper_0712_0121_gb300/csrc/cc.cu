@@ -165,6 +165,7 @@ __device__ __forceinline__ void link_runs(const uint32_t *runs, int a0, int a1, 
 __global__ void __launch_bounds__(CC_THREADS) k_cc_band(RleIn in, int d, int32_t *parent, int *status) {
     __shared__ int32_t sp[CC_CAP];
     __shared__ uint32_t sr[CC_CAP];
+    __shared__ unsigned char sline[CC_CAP];  // band line of each window run
     __shared__ int s_rp[CC_BAND + 1];
     __shared__ int s_sub[CC_BAND + 1];
     __shared__ unsigned char s_gh[CC_BAND];
@@ -214,6 +215,8 @@ __global__ void __launch_bounds__(CC_THREADS) k_cc_band(RleIn in, int d, int32_t
                 sp[i] = i;
                 sr[i] = runs[G + i];
             }
+            for (int l = la - (g > 0 ? 1 : 0) + warp; l < lb; l += CC_WARPS)
+                for (int k = s_rp[l] + (tid & 31); k < s_rp[l + 1]; k += 32) sline[k - G] = (unsigned char)l;
             __syncthreads();
             // one thread per run of the lines whose line above is in the
             // window (balanced over the warps whatever the lines hold), in
@@ -226,8 +229,9 @@ __global__ void __launch_bounds__(CC_THREADS) k_cc_band(RleIn in, int d, int32_t
                 const int k = k0 + tid;
                 if (k0 > s_rp[g > 0 ? la : la + 1]) __syncthreads();
                 if (k >= kend) continue;
-                const int l = band_line(s_rp, nl, k);
-                const int a0 = s_rp[l - 1] - G, a1 = s_rp[l] - G, kk = k - G;
+                const int kk = k - G;
+                const int l = sline[kk];
+                const int a0 = s_rp[l - 1] - G, a1 = s_rp[l] - G;
                 const uint32_t r = sr[kk];
                 const int rs = run_start(r), re = run_end(r);
                 int lo = a0, hi = a1;

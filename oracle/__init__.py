@@ -1,5 +1,5 @@
 """Plain CPU oracle for rectangular binary morphology, run-length coding,
-connected components of RLE images and run-length statistics.
+connected components of RLE images, run-length statistics and transposition.
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
@@ -80,6 +80,8 @@ def _load():
             lib.oracle_rle_component_stats.restype = None
             lib.oracle_run_length_hist.argtypes = [i64p, i64p, i32p, u16p, ci, ci]
             lib.oracle_run_length_hist.restype = None
+            lib.oracle_transpose.argtypes = [u8p, u8p, ci, ci]
+            lib.oracle_transpose.restype = None
             _lib = lib
     return _lib
 
@@ -385,3 +387,20 @@ def run_length_hist(row_ptr, runs, W: int, H: int):
     _load().oracle_run_length_hist(_ptr(black, ctypes.c_int64), _ptr(white, ctypes.c_int64),
                                    _ptr(rp, ctypes.c_int32), _ptr(ru, ctypes.c_uint16), int(W), int(H))
     return black, white
+
+
+# ------------------------------------------------------------ transpose ---
+
+def transpose(img) -> np.ndarray:
+    """The transposed bitmap ``out[x, y] = img[y, x]`` (plain loop in C)."""
+    a = _as_img(img)
+    H, W = a.shape
+    out = np.zeros((W, H), np.uint8)
+    _load().oracle_transpose(_ptr(out, ctypes.c_uint8), _ptr(a, ctypes.c_uint8), W, H)
+    return out
+
+
+def rle_transpose(row_ptr, runs, W: int, H: int):
+    """Transpose of an RLE image (section "Efficient Transpose"):
+    decode, transpose, encode; the result has width H and height W."""
+    return rle_encode(transpose(rle_decode(row_ptr, runs, W, H)))

@@ -1,6 +1,7 @@
 /*
  * Plain CPU oracle for rectangular binary morphology, run-length coding,
- * connected components of RLE images and run-length statistics.
+ * connected components of RLE images, run-length statistics and
+ * transposition.
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call this code:
  * only tests/, the smoke check in __graft_entry__ and the cpu_baseline leg of
@@ -424,4 +425,14 @@ EXPORT void oracle_run_length_hist(int64_t *black, int64_t *white, const int32_t
         }
         if (W > prev_end) white[W - prev_end]++;
     }
+}
+
+/* ---------------------------------------------------------- transpose */
+
+/* Section "Efficient Transpose" (the decode-recode and sweep
+ * algorithms compute this same image): out is H x W (W bytes per row of
+ * the input, H per row of the output), out(y, x) = in(x, y). */
+EXPORT void oracle_transpose(uint8_t *out, const uint8_t *in, int W, int H) {
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++) out[(size_t)x * H + y] = in[(size_t)y * W + x];
 }

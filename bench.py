@@ -366,6 +366,8 @@ def run_probe(args):
     results = []
     if args.probe == "cc":
         return run_probe_cc(args, M, src, Wt, Ht, peak, stream)
+    if args.probe == "xpose":
+        return run_probe_xpose(args, M, src, Wt, Ht, page_bytes, peak, stream)
     for se in args.probe_se.split(","):
         if args.probe == "mask":
             # "d<r>": digital disc of radius r; "WxH": the full rectangle as a mask
@@ -457,6 +459,72 @@ def run_probe_cc(args, M, src, Wt, Ht, peak, stream):
             raise SystemExit(1)
     print(json.dumps({"probe": "cc", "width": Wt, "height": Ht, "runs": n_runs, "peak_gb_s": peak,
                       "results": results}))
+
+
+def run_probe_xpose(args, M, src, Wt, Ht, page_bytes, peak, stream):
+    """Transposition (section "Efficient Transpose") of the stack, or of its
+    first 65535 rows for RLE (the transpose's width must fit 16-bit runs);
+    --probe-se lists "packed", "rle" and "rletH" (a 1 x H erosion done as the
+    H x 1 erosion of the transpose, transposed back, next to the direct RLE
+    erosion).  Algorithmic bytes: the packed page read and written once; for
+    RLE the runs and row offsets of input and output."""
+    import torch
+    results = []
+    for tok in args.probe_se.split(","):
+        extra = {}
+        if tok == "packed":
+            dst = M.Packed.empty(Ht, Wt, 64)
+            fn = lambda: M.transpose(dst, src)  # noqa: E731
+            W, H, alg = Wt, Ht, 2 * page_bytes
+        else:
+            H = min(Ht, 65535)
+            W = Wt
+            sub = M.Packed(src.words[:H], Wt)
+            a = M.Rle.empty(W, H, H * args.rle_runs_per_row)
+            M.rle_from_bitmap(a, sub)
+            n_in = int(a.n_runs.item())
+            cap_t = W * (H // 2 + 1)
+            t = M.Rle.empty(H, W, cap_t)
+            ws = torch.empty(M.rle_transpose_workspace_size(a), dtype=torch.uint8, device="cuda")
+            M.rle_transpose(t, a, ws)
+            n_out = int(t.n_runs.item())
+            extra = {"runs_in": n_in, "runs_out": n_out}
+            if tok == "rle":
+                fn = lambda: M.rle_transpose(t, a, ws)  # noqa: E731
+                alg = 4 * (n_in + n_out) + 4 * (H + 1) + 4 * (W + 1)
+            else:
+                h = int(tok[4:])
+                t2 = M.Rle.empty(H, W, cap_t)
+                back = M.Rle.empty(W, H, H * args.rle_runs_per_row)
+                ws_b = torch.empty(M.rle_transpose_workspace_size(t2), dtype=torch.uint8, device="cuda")
+                direct = M.Rle.empty(W, H, H * args.rle_runs_per_row)
+                wsd = torch.empty(M.workspace_size("erode", direct, a, 1, h), dtype=torch.uint8,
+                                  device="cuda")
+                wst = torch.empty(M.workspace_size("erode", t2, t, h, 1), dtype=torch.uint8,
+                                  device="cuda")
+
+                def fn():
+                    M.rle_transpose(t, a, ws)
+                    M.morph_rect("erode", t2, t, h, 1, workspace=wst)
+                    M.rle_transpose(back, t2, ws_b)
+                fd = lambda: M.morph_rect("erode", direct, a, 1, h, workspace=wsd)  # noqa: E731
+                fd()
+                torch.cuda.synchronize()
+                extra["direct_ms"] = round(statistics.median(time_launches(fd, args.probe_reps, stream)), 4)
+                alg = 8 * n_in + 4 * (H + 1)
+        fn()
+        torch.cuda.synchronize()
+        ms = statistics.median(time_launches(fn, args.probe_reps, stream))
+        st = M.sync_status()
+        r = {"se": tok, "width": W, "height": H, "ms": round(ms, 4),
+             "gpix_s": round(W * H / ms / 1e6, 1), "alg_gb_s": round(alg / ms / 1e6, 1),
+             "frac": round(alg / ms / 1e6 / peak, 3), "status": st}
+        r.update(extra)
+        results.append(r)
+        if st != M.MORPH_OK:
+            print(json.dumps(r))
+            raise SystemExit(1)
+    print(json.dumps({"probe": "xpose", "peak_gb_s": peak, "results": results}))
 
 
 def run_ours(args):
@@ -664,7 +732,7 @@ def main():
     ap.add_argument("--batch-pages", type=int, default=256)
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--tune-cache", default=os.path.join("/tmp", "morph_tune_cache.json"))
-    ap.add_argument("--probe", choices=["packed", "rle", "mask", "cc"], default=None,
+    ap.add_argument("--probe", choices=["packed", "rle", "mask", "cc", "xpose"], default=None,
                     help="run one standalone op on a tall page stack (ncu target) and exit")
     ap.add_argument("--probe-op", default="erode")
     ap.add_argument("--probe-se", default="3x3")

@@ -217,6 +217,23 @@ MORPH_API morph_status rle_from_bitmap(const morph_image *dst_rle, const morph_i
 MORPH_API morph_status rle_to_bitmap(const morph_image *dst_packed, const morph_image *src_rle,
                            void *stream);
 
+/* ------------------------------------------------------------- transpose --
+ * Section "Efficient Transpose": dst(x, y) = src(y, x).
+ * morph_transpose: packed src (W x H) -> packed dst (H x W), either word
+ * size; padding bits of dst written 0.  No workspace.  A bit-matrix
+ * transpose of 32 x 32 blocks in registers, tiles staged in shared memory.
+ * morph_rle_transpose: RLE src (W x H) -> RLE dst (H x W, so H <= 65535):
+ * the columns of src become the rows of dst (vertical runs, e.g. for
+ * vertical run-length statistics or between-line operations done as
+ * within-line ones).  Runs painted into a bitmap, transposed, encoded again
+ * (capacity rules of rle_from_bitmap).  Workspace (device, 256-byte
+ * aligned): morph_rle_transpose_workspace_size() bytes.
+ * Errors: MORPH_EINVAL (formats, sizes, overlap), MORPH_ENOMEM, MORPH_ECUDA. */
+MORPH_API morph_status morph_transpose(const morph_image *dst, const morph_image *src, void *stream);
+MORPH_API size_t morph_rle_transpose_workspace_size(const morph_image *src_rle);
+MORPH_API morph_status morph_rle_transpose(const morph_image *dst_rle, const morph_image *src_rle,
+                                           void *workspace, size_t workspace_bytes, void *stream);
+
 /* ------------------------------------------------ connected components --
  * Section "Connected Component Extraction and Statistics".
  * morph_rle_components labels every run of an RLE image by its connected

@@ -610,6 +610,58 @@ morph_status morph_run_length_hist(int64_t *black_hist, int64_t *white_hist,
     return MORPH_OK;
 }
 
+morph_status morph_transpose(const morph_image *dst, const morph_image *src, void *stream) {
+    morph_status st = check_image(src, "src");
+    if (st) return st;
+    if ((st = check_image(dst, "dst"))) return st;
+    if (!is_packed(src->fmt) || !is_packed(dst->fmt))
+        return fail(MORPH_EINVAL, "morph_transpose needs packed images (morph_rle_transpose for RLE)");
+    if (dst->width != src->height || dst->height != src->width)
+        return fail(MORPH_EINVAL, "dst is %d x %d, the transpose of %d x %d must be %d x %d", dst->width,
+                    dst->height, src->width, src->height, src->height, src->width);
+    if (overlap(packed_range(src), packed_range(dst))) return fail(MORPH_EINVAL, "dst overlaps src");
+    const int nw_out = dst->fmt == MORPH_PACKED32 ? (dst->width + 31) / 32 : 2 * ((dst->width + 63) / 64);
+    cudaError_t e = launch_transpose((const uint32_t *)src->words, src->stride_words * (word_bits(src->fmt) / 32),
+                                     src->width, src->height, (uint32_t *)dst->words,
+                                     dst->stride_words * (word_bits(dst->fmt) / 32), nw_out,
+                                     (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "transpose launch");
+    return MORPH_OK;
+}
+
+size_t morph_rle_transpose_workspace_size(const morph_image *src_rle) {
+    if (!src_rle || src_rle->fmt != MORPH_RLE || src_rle->width < 1 || src_rle->height < 1) return 0;
+    return rle_transpose_ws_bytes(src_rle->width, src_rle->height);
+}
+
+morph_status morph_rle_transpose(const morph_image *dst_rle, const morph_image *src_rle, void *workspace,
+                                 size_t workspace_bytes, void *stream) {
+    morph_status st = check_image(src_rle, "src");
+    if (st) return st;
+    if ((st = check_image(dst_rle, "dst"))) return st;
+    if (src_rle->fmt != MORPH_RLE || dst_rle->fmt != MORPH_RLE)
+        return fail(MORPH_EINVAL, "morph_rle_transpose needs RLE images (morph_transpose for packed)");
+    if (dst_rle->width != src_rle->height || dst_rle->height != src_rle->width)
+        return fail(MORPH_EINVAL, "dst is %d x %d, the transpose of %d x %d must be %d x %d",
+                    dst_rle->width, dst_rle->height, src_rle->width, src_rle->height,
+                    src_rle->height, src_rle->width);
+    const Range srp{(uintptr_t)src_rle->row_ptr, (uintptr_t)(src_rle->row_ptr + src_rle->height + 1)};
+    const Range sru{(uintptr_t)src_rle->runs, (uintptr_t)(src_rle->runs + 2 * src_rle->capacity_runs)};
+    const Range drp{(uintptr_t)dst_rle->row_ptr, (uintptr_t)(dst_rle->row_ptr + dst_rle->height + 1)};
+    const Range dru{(uintptr_t)dst_rle->runs, (uintptr_t)(dst_rle->runs + 2 * dst_rle->capacity_runs)};
+    if (overlap(drp, srp) || overlap(drp, sru) || overlap(dru, srp) || overlap(dru, sru))
+        return fail(MORPH_EINVAL, "dst overlaps src");
+    const size_t need = rle_transpose_ws_bytes(src_rle->width, src_rle->height);
+    if (!workspace || workspace_bytes < need)
+        return fail(MORPH_ENOMEM, "the transpose needs %zu bytes of workspace, got %zu", need,
+                    workspace ? workspace_bytes : (size_t)0);
+    if ((uintptr_t)workspace % 256) return fail(MORPH_EINVAL, "workspace is not 256-byte aligned");
+    cudaError_t e = launch_rle_transpose(rle_in(src_rle), rle_out(dst_rle), workspace, device_status_ptr(),
+                                         (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "RLE transpose launch");
+    return MORPH_OK;
+}
+
 morph_status morph_sync_status(void *stream) {
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");

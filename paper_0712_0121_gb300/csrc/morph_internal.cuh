@@ -173,6 +173,15 @@ struct MorphCC {
 cudaError_t launch_rle_components(RleIn in, int conn, MorphCC c, int *status, cudaStream_t s);
 cudaError_t launch_run_length_hist(RleIn in, int64_t *black, int64_t *white, cudaStream_t s);
 
+// Transposition (transpose.cu): packed src (H rows, pixels x < W) -> packed
+// dst (W rows, nw_out words per row written, words past ceil(H/32) zero).
+cudaError_t launch_transpose(const uint32_t *src, int64_t sstride, int W, int H, uint32_t *dst,
+                             int64_t dstride, int nw_out, cudaStream_t s);
+// RLE transpose through two bitmaps in ws (rle_transpose_ws_bytes(W, H)
+// bytes, 256-byte aligned); out has width H and height W.
+size_t rle_transpose_ws_bytes(int W, int H);
+cudaError_t launch_rle_transpose(RleIn in, RleOut out, void *ws, int *status, cudaStream_t s);
+
 cudaError_t launch_rle_from_bitmap(const uint32_t *src, int64_t sstride, int W, int H,
                                    RleOut out, int32_t *counts, int *status, cudaStream_t s);
 cudaError_t launch_rle_to_bitmap(RleIn in, uint32_t *dst, int64_t dstride, int nw_cover,

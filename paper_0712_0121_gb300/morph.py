@@ -92,6 +92,12 @@ def _load():
     lib.rle_from_bitmap.restype = ci
     lib.rle_to_bitmap.argtypes = [img_p, img_p, vp]
     lib.rle_to_bitmap.restype = ci
+    lib.morph_transpose.argtypes = [img_p, img_p, vp]
+    lib.morph_transpose.restype = ci
+    lib.morph_rle_transpose_workspace_size.argtypes = [img_p]
+    lib.morph_rle_transpose_workspace_size.restype = sz
+    lib.morph_rle_transpose.argtypes = [img_p, img_p, vp, sz, vp]
+    lib.morph_rle_transpose.restype = ci
     lib.morph_components_workspace_size.argtypes = [img_p]
     lib.morph_components_workspace_size.restype = sz
     lib.morph_rle_components.argtypes = [vp, vp, ctypes.c_int64, vp, img_p, ci, vp, sz, vp]
@@ -365,6 +371,28 @@ def rle_from_bitmap(dst: Rle, src: Packed, workspace: torch.Tensor | None = None
 def rle_to_bitmap(dst: Packed, src: Rle, stream=None) -> None:
     _check(_lib.rle_to_bitmap(ctypes.byref(dst.desc()), ctypes.byref(src.desc()),
                               _stream_handle(stream)))
+
+
+# ------------------------------------------------------------ transpose
+
+def transpose(dst: Packed, src: Packed, stream=None) -> None:
+    """dst (H x W) = transpose of packed src (W x H)."""
+    _check(_lib.morph_transpose(ctypes.byref(dst.desc()), ctypes.byref(src.desc()),
+                                _stream_handle(stream)))
+
+
+def rle_transpose_workspace_size(src: Rle) -> int:
+    return int(_lib.morph_rle_transpose_workspace_size(ctypes.byref(src.desc())))
+
+
+def rle_transpose(dst: Rle, src: Rle, workspace: torch.Tensor | None = None, stream=None) -> None:
+    """dst (H x W, RLE) = transpose of RLE src (W x H): the columns of src as rows."""
+    if workspace is None:
+        workspace = torch.empty(max(rle_transpose_workspace_size(src), 1), dtype=torch.uint8,
+                                device=src.row_ptr.device)
+    wp, wn = _ws_args(workspace)
+    _check(_lib.morph_rle_transpose(ctypes.byref(dst.desc()), ctypes.byref(src.desc()), wp, wn,
+                                    _stream_handle(stream)))
 
 
 # ------------------------------------------------- connected components

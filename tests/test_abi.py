@@ -150,3 +150,29 @@ def test_components_and_histogram_checks(M):
     assert L.morph_run_length_hist(hb, hb + 8, ctypes.byref(src), None) == M.MORPH_EINVAL  # overlap
     assert L.morph_run_length_hist(hb + 4, hw, ctypes.byref(src), None) == M.MORPH_EINVAL  # misaligned
     assert L.morph_run_length_hist(None, None, ctypes.byref(src), None) == M.MORPH_OK      # nothing to do
+
+
+def test_transpose_checks(M):
+    L = M.lib()
+    src = _img(M, W=100, H=10, words=0x10000, stride=2)
+    good = _img(M, W=10, H=100, words=0x90000, stride=1)
+    bad = _img(M, W=100, H=10, words=0x90000, stride=2)
+    assert L.morph_transpose(ctypes.byref(bad), ctypes.byref(src), None) == M.MORPH_EINVAL  # not transposed sizes
+    assert b"transpose" in L.morph_last_error()
+    over = _img(M, W=10, H=100, words=0x10000 + 8, stride=1)
+    assert L.morph_transpose(ctypes.byref(over), ctypes.byref(src), None) == M.MORPH_EINVAL  # overlap
+
+    def rle(W, H, rp, runs, cap=100):
+        d = M.morph_image()
+        d.fmt, d.width, d.height = 2, W, H
+        d.row_ptr, d.runs, d.capacity_runs = rp, runs, cap
+        return d
+    rs = rle(100, 10, 0x1000, 0x2000)
+    rd = rle(10, 100, 0x5000, 0x6000)
+    need = L.morph_rle_transpose_workspace_size(ctypes.byref(rs))
+    assert need >= 10 * 4 * 4 + 100 * 4 + 100 * 4
+    assert L.morph_transpose(ctypes.byref(rd), ctypes.byref(rs), None) == M.MORPH_EINVAL  # RLE to packed entry
+    assert L.morph_rle_transpose(ctypes.byref(rd), ctypes.byref(rs), None, 0, None) == M.MORPH_ENOMEM
+    assert L.morph_rle_transpose(ctypes.byref(rd), ctypes.byref(rs), 0x900010, need, None) == M.MORPH_EINVAL
+    assert L.morph_rle_transpose(ctypes.byref(rs), ctypes.byref(rs), 0x900000, need, None) == M.MORPH_EINVAL
+    assert L.morph_rle_transpose(ctypes.byref(good), ctypes.byref(rs), 0x900000, need, None) == M.MORPH_EINVAL

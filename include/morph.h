@@ -3,8 +3,10 @@
  *
  * Binary erosion, dilation, opening and closing with rectangular structuring
  * elements (SEs) on packed bitmaps and on row-wise run-length (RLE) images,
- * and the conversions between the two formats (Breuel, "Efficient Binary and
- * Run Length Morphology and its Application to Document Image Processing").
+ * the conversions between the two formats, arbitrary structuring elements on
+ * packed bitmaps, transposition, connected components with per-component
+ * statistics and run-length histograms (Breuel, "Efficient Binary and Run
+ * Length Morphology and its Application to Document Image Processing").
  *
  * Every buffer named here is DEVICE memory owned by the caller; the library
  * never allocates device memory.  Scratch space, where an operation needs it,

@@ -1,5 +1,6 @@
 """Plain CPU oracle for rectangular binary morphology, run-length coding,
-connected components of RLE images, run-length statistics and transposition.
+connected components of RLE images, run-length statistics, transposition
+and sheared line structuring elements.
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
@@ -82,6 +83,8 @@ def _load():
             lib.oracle_run_length_hist.restype = None
             lib.oracle_transpose.argtypes = [u8p, u8p, ci, ci]
             lib.oracle_transpose.restype = None
+            lib.oracle_sheared_line.argtypes = [u8p, u8p, ci, ci, i32p, ci, ci, ci]
+            lib.oracle_sheared_line.restype = None
             _lib = lib
     return _lib
 
@@ -404,3 +407,39 @@ def rle_transpose(row_ptr, runs, W: int, H: int):
     """Transpose of an RLE image (section "Efficient Transpose"):
     decode, transpose, encode; the result has width H and height W."""
     return rle_encode(transpose(rle_decode(row_ptr, runs, W, H)))
+
+
+# --------------------------------------------------- sheared line SEs ---
+
+def sheared_line(op: str, img, shift, length: int, origin: int, horizontal: bool = False) -> np.ndarray:
+    """Erode / dilate / open / close by a line sheared by ``shift`` (section
+    "Morphology with Lines at Arbitrary Orientations"): skew, axis-parallel
+    line of ``length`` pixels with origin ``origin``, skew back, written out
+    pixel by pixel (see ``oracle_sheared_line``).  ``horizontal``: the line
+    runs along the rows and ``shift[x]`` moves column x down (the transposed
+    case)."""
+    a = _as_img(img)
+    if horizontal:
+        return transpose(sheared_line(op, transpose(a), shift, length, origin, False))
+    H, W = a.shape
+    sh = np.ascontiguousarray(shift, dtype=np.int32)
+    if sh.shape != (H,):
+        raise ValueError("one shift per line")
+    if not (1 <= length and 0 <= origin < length):
+        raise ValueError("bad line")
+
+    def one(x, dil):
+        out = np.zeros_like(x)
+        _load().oracle_sheared_line(_ptr(out, ctypes.c_uint8), _ptr(x, ctypes.c_uint8), W, H,
+                                    _ptr(sh, ctypes.c_int32), int(length), int(origin), int(dil))
+        return out
+    if op == "erode":
+        return one(a, 0)
+    if op == "dilate":
+        return one(a, 1)
+    if op == "open":
+        return one(one(a, 0), 1)
+    if op == "close":
+        return one(one(a, 1), 0)
+    raise ValueError(op)
+

@@ -436,3 +436,36 @@ EXPORT void oracle_transpose(uint8_t *out, const uint8_t *in, int W, int H) {
     for (int y = 0; y < H; y++)
         for (int x = 0; x < W; x++) out[(size_t)x * H + y] = in[(size_t)y * W + x];
 }
+
+/* --------------------------------------------------- sheared line SEs */
+
+/* Section "Morphology with Lines at Arbitrary Orientations": a line at an
+ * angle is eroded by skewing the image perpendicular to the erosion,
+ * eroding by an axis-parallel line and skewing back.  Written out: line y
+ * is shifted right by shift[y] (the skew), the vertical line of `length`
+ * rows with origin o is applied (clipped window, as for the rectangles:
+ * positions that hold no image pixel are left out), and the lines are
+ * shifted back.  Pixel by pixel that is
+ *   E(x,y) = AND over j in [-o, length-1-o] of I(x + shift[y] - shift[y+j], y+j)
+ *   D(x,y) = OR  over j in [-(length-1-o), o] of the same,
+ * each term only where 0 <= y+j < H and 0 <= x + shift[y] - shift[y+j] < W.
+ * dilate = 0 erodes, 1 dilates. */
+EXPORT void oracle_sheared_line(uint8_t *out, const uint8_t *in, int W, int H,
+                                const int32_t *shift, int length, int o, int dilate) {
+    const int j0 = dilate ? -(length - 1 - o) : -o;
+    const int j1 = dilate ? o : length - 1 - o;
+    for (int y = 0; y < H; y++) {
+        for (int x = 0; x < W; x++) {
+            int v = dilate ? 0 : 1;
+            for (int j = j0; j <= j1; j++) {
+                const int yy = y + j;
+                if (yy < 0 || yy >= H) continue;
+                const long xx = (long)x + shift[y] - shift[yy];
+                if (xx < 0 || xx >= W) continue;
+                const int p = in[(size_t)yy * W + xx];
+                if (dilate ? p : !p) { v = dilate; break; }
+            }
+            out[(size_t)y * W + x] = (uint8_t)v;
+        }
+    }
+}

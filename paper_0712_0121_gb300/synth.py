@@ -169,3 +169,9 @@ def config4_jobs(n: int = 256, seed: int = seed_for(4, 0)):
 
 def config4_page(job):
     return document_page(job["W"], job["H"], job["seed"], job["density"])
+
+
+def line_shifts(n: int, slope: float) -> np.ndarray:
+    """Skew table of a line with the given slope (pixels across per pixel
+    along): shift[i] = floor(i * slope + 1/2), the nearest integer."""
+    return np.floor(np.arange(n) * float(slope) + 0.5).astype(np.int32)

@@ -366,6 +366,8 @@ def run_probe(args):
     results = []
     if args.probe == "cc":
         return run_probe_cc(args, M, src, Wt, Ht, peak, stream)
+    if args.probe == "line":
+        return run_probe_line(args, M, src, Wt, Ht, page_bytes, peak, stream)
     if args.probe == "xpose":
         return run_probe_xpose(args, M, src, Wt, Ht, page_bytes, peak, stream)
     for se in args.probe_se.split(","):
@@ -459,6 +461,36 @@ def run_probe_cc(args, M, src, Wt, Ht, peak, stream):
             raise SystemExit(1)
     print(json.dumps({"probe": "cc", "width": Wt, "height": Ht, "runs": n_runs, "peak_gb_s": peak,
                       "results": results}))
+
+
+def run_probe_line(args, M, src, Wt, Ht, page_bytes, peak, stream):
+    """Line elements of half length 12 at the angles (degrees) listed in
+    --probe-se, --probe-op erode / dilate / open / close, on the stack
+    (skew, axis-parallel line, skew back; the transposed case for lines
+    nearer the x axis).  Algorithmic bytes: the page read and written once."""
+    import torch
+    results = []
+    dst = M.Packed.empty(Wt, Ht, 64)
+    for tok in args.probe_se.split(","):
+        angle = float(tok)
+        shift, L, o, horizontal = M.line_element(angle, 12, Wt, Ht)
+        n = M.sheared_line_workspace_size(args.probe_op, src, shift, L, horizontal)
+        ws = torch.empty(n, dtype=torch.uint8, device="cuda")
+        fn = lambda: M.sheared_line(args.probe_op, dst, src, shift, L, o, horizontal,  # noqa: E731
+                                    workspace=ws)
+        fn()
+        torch.cuda.synchronize()
+        ms = statistics.median(time_launches(fn, args.probe_reps, stream))
+        st = M.sync_status()
+        alg = 2 * page_bytes
+        results.append({"se": tok, "length": L, "horizontal": bool(horizontal), "ms": round(ms, 4),
+                        "gpix_s": round(Wt * Ht / ms / 1e6, 1), "alg_gb_s": round(alg / ms / 1e6, 1),
+                        "frac": round(alg / ms / 1e6 / peak, 3), "status": st})
+        if st != M.MORPH_OK:
+            print(json.dumps(results[-1]))
+            raise SystemExit(1)
+    print(json.dumps({"probe": "line", "op": args.probe_op, "width": Wt, "height": Ht,
+                      "peak_gb_s": peak, "results": results}))
 
 
 def run_probe_xpose(args, M, src, Wt, Ht, page_bytes, peak, stream):
@@ -732,7 +764,7 @@ def main():
     ap.add_argument("--batch-pages", type=int, default=256)
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--tune-cache", default=os.path.join("/tmp", "morph_tune_cache.json"))
-    ap.add_argument("--probe", choices=["packed", "rle", "mask", "cc", "xpose"], default=None,
+    ap.add_argument("--probe", choices=["packed", "rle", "mask", "cc", "xpose", "line"], default=None,
                     help="run one standalone op on a tall page stack (ncu target) and exit")
     ap.add_argument("--probe-op", default="erode")
     ap.add_argument("--probe-se", default="3x3")

@@ -4,8 +4,9 @@
  * Binary erosion, dilation, opening and closing with rectangular structuring
  * elements (SEs) on packed bitmaps and on row-wise run-length (RLE) images,
  * the conversions between the two formats, arbitrary structuring elements on
- * packed bitmaps, transposition, connected components with per-component
- * statistics and run-length histograms (Breuel, "Efficient Binary and Run
+ * packed bitmaps, line elements at arbitrary angles, transposition,
+ * connected components with per-component statistics and run-length
+ * histograms (Breuel, "Efficient Binary and Run
  * Length Morphology and its Application to Document Image Processing").
  *
  * Every buffer named here is DEVICE memory owned by the caller; the library
@@ -218,6 +219,32 @@ MORPH_API morph_status rle_from_bitmap(const morph_image *dst_rle, const morph_i
                              void *workspace, size_t workspace_bytes, void *stream);
 MORPH_API morph_status rle_to_bitmap(const morph_image *dst_packed, const morph_image *src_rle,
                            void *stream);
+
+/* ------------------------------------------------------ sheared lines --
+ * Section "Morphology with Lines at Arbitrary Orientations": a line element
+ * at an angle is applied by skewing the image perpendicular to the line,
+ * applying the axis-parallel line and skewing back.  Here the skew is given
+ * as a table (for an angle a from the vertical, shift[y] = round(y tan a)):
+ * line y is moved right by shift[y], the vertical line of `length` pixels
+ * with origin `origin` is applied (clipped window: positions holding no
+ * image pixel are left out), and the lines are moved back.  Pixel by pixel
+ *   erode:  E(x,y) = AND over j in [-origin, length-1-origin] of
+ *                    src(x + shift[y] - shift[y+j], y + j)
+ *   dilate: D(x,y) = OR over j in [-(length-1-origin), origin] of the same,
+ * terms only where the source pixel lies in the image; open = D(E), close =
+ * E(D).  horizontal = 1 is the transposed case (shift[x] moves column x
+ * down, the line runs along the rows; n_shift = width), else n_shift =
+ * height.  shift: HOST int32[n_shift], read during the call.  src and dst
+ * packed (either word size), same size, not overlapping.  Workspace
+ * (device, 256-byte aligned): morph_sheared_line_workspace_size() bytes
+ * (0 for invalid arguments).  Errors: MORPH_EINVAL, MORPH_ENOMEM,
+ * MORPH_ECUDA. */
+MORPH_API size_t morph_sheared_line_workspace_size(int op, const morph_image *src, const int32_t *shift,
+                                                   int n_shift, int length, int horizontal);
+MORPH_API morph_status morph_sheared_line(int op, const morph_image *dst, const morph_image *src,
+                                          const int32_t *shift, int n_shift, int length, int origin,
+                                          int horizontal, void *workspace, size_t workspace_bytes,
+                                          void *stream);
 
 /* ------------------------------------------------------------- transpose --
  * Section "Efficient Transpose": dst(x, y) = src(y, x).

@@ -6,6 +6,8 @@
 #include <mutex>
 
 #include "mask.cuh"
+#include <vector>
+
 #include "morph_internal.cuh"
 
 namespace morph {
@@ -345,6 +347,99 @@ size_t mask_ws_bytes(int op, int W, int H, int nlev) {
     return n;
 }
 
+// ---- sheared line elements: skew, vertical line, skew back
+// The skew runs per band of lines, each band in its own canvas with its own
+// base shift, so a canvas is only as much wider than the image as the
+// shifts vary across one band (a skew of the whole image at once would need
+// a canvas wider by the shift range of the whole height).  Bands carry
+// L - 1 halo lines above and below, enough for either stage's window.
+constexpr int LINE_MAX_SPAN = 1 << 20;
+
+struct LinePlan {
+    int band, halo, nb, brows, span;
+};
+
+LinePlan line_plan(int H, int L, const int32_t *shift, std::vector<int32_t> *base) {
+    LinePlan p;
+    p.band = 4 * L > 512 ? 4 * L : 512;
+    if (p.band > H) p.band = H;
+    p.halo = L - 1;
+    p.nb = (H + p.band - 1) / p.band;
+    p.brows = p.band + 2 * p.halo;
+    p.span = 0;
+    if (base) base->assign(p.nb, 0);
+    for (int b = 0; b < p.nb; ++b) {
+        const int y0 = b * p.band - p.halo < 0 ? 0 : b * p.band - p.halo;
+        const int y1 = b * p.band + p.band + p.halo > H ? H : b * p.band + p.band + p.halo;
+        int lo = shift[y0], hi = shift[y0];
+        for (int y = y0 + 1; y < y1; ++y) {
+            lo = shift[y] < lo ? shift[y] : lo;
+            hi = shift[y] > hi ? shift[y] : hi;
+        }
+        if (base) (*base)[b] = lo;
+        const int64_t sp = (int64_t)hi - lo;
+        p.span = sp > LINE_MAX_SPAN ? LINE_MAX_SPAN + 1 : (sp > p.span ? (int)sp : p.span);
+    }
+    return p;
+}
+
+size_t line_ws_vertical(int op, int W, int H, const LinePlan &p) {
+    const size_t nwc = ((size_t)W + p.span + 31) / 32, nw = ((size_t)W + 31) / 32;
+    const size_t crows = (size_t)p.nb * p.brows;
+    size_t n = align256((size_t)H * 4) + align256((size_t)p.nb * 4) + 2 * align256(crows * nwc * 4);
+    if (op == MORPH_OPEN || op == MORPH_CLOSE) n += align256((size_t)H * nw * 4);
+    return n;
+}
+
+// W x H: the image the vertical procedure runs on (the transpose for
+// horizontal lines)
+size_t line_ws(int op, int W, int H, const LinePlan &p, int horizontal) {
+    if (!horizontal) return line_ws_vertical(op, W, H, p);
+    const size_t nwt = ((size_t)W + 31) / 32;  // rows of the transposed image
+    return 2 * align256((size_t)H * nwt * 4) + line_ws_vertical(op, W, H, p);
+}
+
+// One stage (erode or dilate) of u32 rows: skew into the band canvases A
+// (fill = the value the clipped window ignores), vertical line A -> B,
+// skew back to dst.
+cudaError_t line_stage(bool dil, const uint32_t *src, int64_t sst, uint32_t *dst, int64_t dstride,
+                       int dst_cover, int W, int H, const int32_t *dshift, const int32_t *dbase,
+                       const LinePlan &p, int L, int o, uint32_t *A, uint32_t *B, cudaStream_t s) {
+    const int Wc = W + p.span, nwc = (Wc + 31) / 32, crows = p.nb * p.brows;
+    cudaError_t e = launch_shift_rows(src, sst, W, A, nwc, Wc, nwc, crows, H, dshift, dbase, p.band, p.halo, 1,
+                                      dil ? 0u : ONES, s);
+    if (e != cudaSuccess) return e;
+    e = packed_launch(dil ? MORPH_DILATE : MORPH_ERODE, Wc, crows, PackedBuf{A, nwc, B, nwc, nwc},
+                      clip_se(Wc, crows, 1, L, 0, o), s);
+    if (e != cudaSuccess) return e;
+    return launch_shift_rows(B, nwc, Wc, dst, dstride, W, dst_cover, H, H, dshift, dbase, p.band, p.halo, -1,
+                             0u, s);
+}
+
+// The sheared vertical line on a W x H image of u32 rows; ws holds
+// line_ws_vertical(op, W, H, p) bytes.
+cudaError_t line_vertical(int op, const uint32_t *src, int64_t sst, uint32_t *dst, int64_t dstride,
+                          int dst_cover, int W, int H, const int32_t *shift, const LinePlan &p,
+                          const std::vector<int32_t> &base, int L, int o, char *ws, cudaStream_t s) {
+    const size_t nwc = ((size_t)W + p.span + 31) / 32, nw = ((size_t)W + 31) / 32;
+    const size_t crows = (size_t)p.nb * p.brows;
+    int32_t *dshift = (int32_t *)ws;
+    int32_t *dbase = (int32_t *)(ws + align256((size_t)H * 4));
+    uint32_t *A = (uint32_t *)((char *)dbase + align256((size_t)p.nb * 4));
+    uint32_t *B = (uint32_t *)((char *)A + align256(crows * nwc * 4));
+    uint32_t *T = (uint32_t *)((char *)B + align256(crows * nwc * 4));
+    cudaError_t e = cudaMemcpyAsync(dshift, shift, (size_t)H * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dbase, base.data(), (size_t)p.nb * 4, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    if (op == MORPH_ERODE || op == MORPH_DILATE)
+        return line_stage(op == MORPH_DILATE, src, sst, dst, dstride, dst_cover, W, H, dshift, dbase, p, L, o,
+                          A, B, s);
+    const bool dil0 = op == MORPH_CLOSE;
+    e = line_stage(dil0, src, sst, T, (int64_t)nw, (int)nw, W, H, dshift, dbase, p, L, o, A, B, s);
+    if (e != cudaSuccess) return e;
+    return line_stage(!dil0, T, (int64_t)nw, dst, dstride, dst_cover, W, H, dshift, dbase, p, L, o, A, B, s);
+}
+
 }  // namespace
 
 void set_error(const char *fmt, ...) {
@@ -659,6 +754,72 @@ morph_status morph_rle_transpose(const morph_image *dst_rle, const morph_image *
     cudaError_t e = launch_rle_transpose(rle_in(src_rle), rle_out(dst_rle), workspace, device_status_ptr(),
                                          (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "RLE transpose launch");
+    return MORPH_OK;
+}
+
+size_t morph_sheared_line_workspace_size(int op, const morph_image *src, const int32_t *shift,
+                                         int n_shift, int length, int horizontal) {
+    if (!src || src->width < 1 || src->height < 1 || !shift || op < MORPH_ERODE || op > MORPH_CLOSE ||
+        length < 1)
+        return 0;
+    if (n_shift != (horizontal ? src->width : src->height)) return 0;
+    // the vertical procedure runs on the transpose for horizontal lines
+    const int W = horizontal ? src->height : src->width, H = n_shift;
+    const LinePlan p = line_plan(H, length, shift, nullptr);
+    if (p.span > LINE_MAX_SPAN) return 0;
+    return line_ws(op, W, H, p, horizontal);
+}
+
+morph_status morph_sheared_line(int op, const morph_image *dst, const morph_image *src, const int32_t *shift,
+                                int n_shift, int length, int origin, int horizontal, void *workspace,
+                                size_t workspace_bytes, void *stream) {
+    morph_status st = check_image(src, "src");
+    if (st) return st;
+    if ((st = check_image(dst, "dst"))) return st;
+    if (op < MORPH_ERODE || op > MORPH_CLOSE) return fail(MORPH_EINVAL, "op %d is not erode/dilate/open/close", op);
+    if (!is_packed(src->fmt) || !is_packed(dst->fmt)) return fail(MORPH_EINVAL, "sheared lines need packed images");
+    if (dst->width != src->width || dst->height != src->height) return fail(MORPH_EINVAL, "dst and src sizes differ");
+    if (overlap(packed_range(src), packed_range(dst))) return fail(MORPH_EINVAL, "dst overlaps src");
+    const int W = src->width, H = src->height;
+    if (!shift) return fail(MORPH_EINVAL, "shift is NULL");
+    if (n_shift != (horizontal ? W : H))
+        return fail(MORPH_EINVAL, "n_shift %d: one shift per %s needed (%d)", n_shift, horizontal ? "column" : "line",
+                    horizontal ? W : H);
+    if (length < 1 || origin < 0 || origin >= length)
+        return fail(MORPH_EINVAL, "line of length %d with origin %d", length, origin);
+    // the vertical procedure's image: the transpose for horizontal lines
+    const int Wv = horizontal ? H : W, Hv = n_shift;
+    std::vector<int32_t> base;
+    const LinePlan p = line_plan(Hv, length, shift, &base);
+    if (p.span > LINE_MAX_SPAN)
+        return fail(MORPH_EINVAL, "shifts vary by more than %d pixels within one band", LINE_MAX_SPAN);
+    const size_t need = line_ws(op, Wv, Hv, p, horizontal);
+    if (!workspace || workspace_bytes < need)
+        return fail(MORPH_ENOMEM, "the sheared line needs %zu bytes of workspace, got %zu", need,
+                    workspace ? workspace_bytes : (size_t)0);
+    if ((uintptr_t)workspace % 256) return fail(MORPH_EINVAL, "workspace is not 256-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint32_t *sw = (const uint32_t *)src->words;
+    const int64_t sst = src->stride_words * (word_bits(src->fmt) / 32);
+    uint32_t *dw = (uint32_t *)dst->words;
+    const int64_t dstride = dst->stride_words * (word_bits(dst->fmt) / 32);
+    const int cover = dst->fmt == MORPH_PACKED32 ? (W + 31) / 32 : 2 * ((W + 63) / 64);
+    cudaError_t e;
+    if (!horizontal) {
+        e = line_vertical(op, sw, sst, dw, dstride, cover, W, H, shift, p, base, length, origin,
+                          (char *)workspace, s);
+    } else {
+        // the transposed case: columns skewed, the line along the rows
+        const int nwt = (H + 31) / 32;
+        uint32_t *XT = (uint32_t *)workspace;
+        uint32_t *XD = (uint32_t *)((char *)workspace + align256((size_t)W * nwt * 4));
+        char *rest = (char *)XD + align256((size_t)W * nwt * 4);
+        e = launch_transpose(sw, sst, W, H, XT, nwt, nwt, s);
+        if (e == cudaSuccess)
+            e = line_vertical(op, XT, nwt, XD, nwt, nwt, H, W, shift, p, base, length, origin, rest, s);
+        if (e == cudaSuccess) e = launch_transpose(XD, nwt, H, W, dw, dstride, cover, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "sheared line launch");
     return MORPH_OK;
 }
 

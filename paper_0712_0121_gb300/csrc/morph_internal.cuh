@@ -182,6 +182,17 @@ cudaError_t launch_transpose(const uint32_t *src, int64_t sstride, int W, int H,
 size_t rle_transpose_ws_bytes(int W, int H);
 cudaError_t launch_rle_transpose(RleIn in, RleOut out, void *ws, int *status, cudaStream_t s);
 
+// Skew into / out of a stack of band canvases (skew.cu).  Band b of `band`
+// image lines has `halo` extra lines above and below (fill rows outside the
+// image) and moves line y right by shift[y] - base[b] (device arrays).
+// sign > 0: image (src) -> canvases (dst, `rows` = bands * (band + 2 halo));
+// sign < 0: canvases (src) -> image (dst, `rows` = H).  Source positions
+// outside [0, src_bits) read as fill; dst bits at p >= dst_bits written 0.
+cudaError_t launch_shift_rows(const uint32_t *src, int64_t sstride, int src_bits, uint32_t *dst,
+                              int64_t dstride, int dst_bits, int nw_dst, int rows, int H, const int32_t *shift,
+                              const int32_t *base, int band, int halo, int sign, uint32_t fill,
+                              cudaStream_t s);
+
 cudaError_t launch_rle_from_bitmap(const uint32_t *src, int64_t sstride, int W, int H,
                                    RleOut out, int32_t *counts, int *status, cudaStream_t s);
 cudaError_t launch_rle_to_bitmap(RleIn in, uint32_t *dst, int64_t dstride, int nw_cover,

@@ -15,6 +15,7 @@ Images:
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 
 import numpy as np
@@ -92,6 +93,11 @@ def _load():
     lib.rle_from_bitmap.restype = ci
     lib.rle_to_bitmap.argtypes = [img_p, img_p, vp]
     lib.rle_to_bitmap.restype = ci
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    lib.morph_sheared_line_workspace_size.argtypes = [ci, img_p, i32p, ci, ci, ci]
+    lib.morph_sheared_line_workspace_size.restype = sz
+    lib.morph_sheared_line.argtypes = [ci, img_p, img_p, i32p, ci, ci, ci, ci, vp, sz, vp]
+    lib.morph_sheared_line.restype = ci
     lib.morph_transpose.argtypes = [img_p, img_p, vp]
     lib.morph_transpose.restype = ci
     lib.morph_rle_transpose_workspace_size.argtypes = [img_p]
@@ -371,6 +377,52 @@ def rle_from_bitmap(dst: Rle, src: Packed, workspace: torch.Tensor | None = None
 def rle_to_bitmap(dst: Packed, src: Rle, stream=None) -> None:
     _check(_lib.rle_to_bitmap(ctypes.byref(dst.desc()), ctypes.byref(src.desc()),
                               _stream_handle(stream)))
+
+
+# -------------------------------------------------------- sheared lines
+
+def line_element(angle_deg: float, half_length: int, width: int, height: int):
+    """Skew table and line of a line element of half length r at an angle
+    (degrees, counterclockwise from the x axis), as the paper builds it: the
+    skew perpendicular to the erosion is tan of the angle from the line's
+    nearer axis, and the axis-parallel line has 2 round(r cos) + 1 pixels.
+    Returns (shift int32 array, length, origin, horizontal)."""
+    a = (float(angle_deg) + 90.0) % 180.0 - 90.0      # [-90, 90)
+    horizontal = abs(a) <= 45.0
+    # image rows grow downwards: a line rising to the right at angle a has
+    # points (x + i, y - i tan a) (along the rows) or (x - j cot a, y + j)
+    off = a if horizontal else 90.0 - a
+    t = math.tan(math.radians(off))
+    n = width if horizontal else height
+    shift = np.floor(np.arange(n) * t + 0.5).astype(np.int32)
+    c = int(round(half_length * abs(math.cos(math.radians(off)))))
+    return shift, 2 * c + 1, c, horizontal
+
+
+def sheared_line_workspace_size(op, src: Packed, shift, length: int, horizontal: bool = False) -> int:
+    sh = np.ascontiguousarray(shift, dtype=np.int32)
+    return int(_lib.morph_sheared_line_workspace_size(
+        OPS.get(op, op), ctypes.byref(src.desc()), sh.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+        int(sh.shape[0]), int(length), int(bool(horizontal))))
+
+
+def sheared_line(op, dst: Packed, src: Packed, shift, length: int, origin=None, horizontal: bool = False,
+                 workspace: torch.Tensor | None = None, stream=None) -> None:
+    """Erode / dilate / open / close by a line sheared by the table ``shift``
+    (one entry per line, or per column when ``horizontal``): skew, axis-parallel
+    line of ``length`` pixels, skew back.  See ``line_element`` for a table from
+    an angle."""
+    sh = np.ascontiguousarray(shift, dtype=np.int32)
+    o = length // 2 if origin is None else origin
+    opc = OPS.get(op, op)
+    if workspace is None:
+        n = sheared_line_workspace_size(opc, src, sh, length, horizontal)
+        workspace = torch.empty(max(n, 1), dtype=torch.uint8, device=src.words.device)
+    wp, wn = _ws_args(workspace)
+    _check(_lib.morph_sheared_line(opc, ctypes.byref(dst.desc()), ctypes.byref(src.desc()),
+                                   sh.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(sh.shape[0]),
+                                   int(length), int(o), int(bool(horizontal)), wp, wn,
+                                   _stream_handle(stream)))
 
 
 # ------------------------------------------------------------ transpose

@@ -176,3 +176,27 @@ def test_transpose_checks(M):
     assert L.morph_rle_transpose(ctypes.byref(rd), ctypes.byref(rs), 0x900010, need, None) == M.MORPH_EINVAL
     assert L.morph_rle_transpose(ctypes.byref(rs), ctypes.byref(rs), 0x900000, need, None) == M.MORPH_EINVAL
     assert L.morph_rle_transpose(ctypes.byref(good), ctypes.byref(rs), 0x900000, need, None) == M.MORPH_EINVAL
+
+
+def test_sheared_line_checks(M):
+    L = M.lib()
+    i32 = ctypes.c_int32 * 10
+    shift = i32(*range(10))
+    src = _img(M, W=100, H=10, words=0x10000, stride=2)
+    dst = _img(M, W=100, H=10, words=0x90000, stride=2)
+    need = L.morph_sheared_line_workspace_size(0, ctypes.byref(src), shift, 10, 5, 0)
+    assert need > 0 and need % 256 == 0
+    assert L.morph_sheared_line_workspace_size(0, ctypes.byref(src), shift, 9, 5, 0) == 0   # wrong count
+
+    def call(op=0, n=10, length=5, origin=2, horizontal=0, ws=0x900000, nws=need, s=src):
+        return L.morph_sheared_line(op, ctypes.byref(dst), ctypes.byref(s), shift, n, length, origin,
+                                    horizontal, ws, nws, None)
+    assert call(op=7) == M.MORPH_EINVAL
+    assert call(n=9) == M.MORPH_EINVAL
+    assert call(horizontal=1) == M.MORPH_EINVAL          # needs one shift per column (100)
+    assert call(length=0) == M.MORPH_EINVAL
+    assert call(origin=5) == M.MORPH_EINVAL
+    assert call(ws=None) == M.MORPH_ENOMEM
+    assert call(nws=need - 1) == M.MORPH_ENOMEM
+    assert call(ws=0x900010) == M.MORPH_EINVAL           # not 256-byte aligned
+    assert call(s=_img(M, W=100, H=10, words=0x90000 + 8, stride=2)) == M.MORPH_EINVAL  # overlap

@@ -369,6 +369,8 @@ def run_probe(args):
     results = []
     if args.probe == "cc":
         return run_probe_cc(args, M, src, Wt, Ht, peak, stream)
+    if args.probe == "layout":
+        return run_probe_layout(args, M, stream)
     if args.probe == "line":
         return run_probe_line(args, M, src, Wt, Ht, page_bytes, peak, stream)
     if args.probe == "xpose":
@@ -464,6 +466,34 @@ def run_probe_cc(args, M, src, Wt, Ht, peak, stream):
             raise SystemExit(1)
     print(json.dumps({"probe": "cc", "width": Wt, "height": Ht, "runs": n_runs, "peak_gb_s": peak,
                       "results": results}))
+
+
+def run_probe_layout(args, M, stream):
+    """Layout analysis of single letter pages (2550 x 3300), one call per
+    page (each call reads two histograms back to the host), as pages/s over
+    16 distinct pages."""
+    import torch
+    pages = [M.pack(p, 64) for p in make_pages(16)]
+    ws = torch.empty(M.layout_workspace_size(pages[0]), dtype=torch.uint8, device="cuda")
+    boxes = torch.empty((65536, 7), dtype=torch.int64, device="cuda")
+    nb = torch.zeros(1, dtype=torch.int64, device="cuda")
+    found = []
+    for pg in pages:
+        _, _, gaps = M.layout_boxes(pg, 90, boxes=boxes, n_boxes=nb, workspace=ws)
+        found.append((gaps, int(nb.item())))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps = max(1, args.probe_reps)
+    for _ in range(reps):
+        for pg in pages:
+            M.layout_boxes(pg, 90, boxes=boxes, n_boxes=nb, workspace=ws)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / (reps * len(pages))
+    st = M.sync_status()
+    print(json.dumps({"probe": "layout", "width": W, "height": H, "ms_per_page": round(dt * 1e3, 4),
+                      "pages_s": round(1.0 / dt, 1), "gaps_and_blocks": found[:4], "status": st}))
+    if st != M.MORPH_OK:
+        raise SystemExit(1)
 
 
 def run_probe_line(args, M, src, Wt, Ht, page_bytes, peak, stream):
@@ -821,7 +851,7 @@ def main():
     ap.add_argument("--batch-pages", type=int, default=256)
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--tune-cache", default=os.path.join("/tmp", "morph_tune_cache.json"))
-    ap.add_argument("--probe", choices=["packed", "rle", "mask", "cc", "xpose", "line"], default=None,
+    ap.add_argument("--probe", choices=["packed", "rle", "mask", "cc", "xpose", "line", "layout"], default=None,
                     help="run one standalone op on a tall page stack (ncu target) and exit")
     ap.add_argument("--probe-op", default="erode")
     ap.add_argument("--probe-se", default="3x3")

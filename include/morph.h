@@ -300,6 +300,26 @@ MORPH_API morph_status morph_rle_components(int32_t *labels, morph_component *st
                                             void *workspace, size_t workspace_bytes,
                                             void *stream);
 
+/* Layout analysis (section "Document Analysis Performance"): the spacing of
+ * words and of lines is estimated from the white run lengths along the lines
+ * and along the columns (via the transpose): the gap estimate is the
+ * smallest length L such that white runs of length <= L make up at least
+ * coverage_pct percent of the white runs no longer than 1/16 of the line
+ * (0 without such runs).  The page is dilated by a (gap_h + 1) x (gap_v + 1)
+ * rectangle (origin at its centre), merging characters and lines into
+ * blocks, and the 8-connected components of the result are returned as
+ * records in `boxes` (as morph_rle_components, max_boxes of them; the count
+ * in *n_boxes on the device).  gaps (HOST int32[2], may be NULL) receives
+ * gap_h and gap_v.  page: packed, both sides <= 65535.  Synchronises the
+ * stream once (the two histograms are read back to choose the rectangle).
+ * Workspace (device, 256-byte aligned): morph_layout_workspace_size() bytes.
+ * Errors: MORPH_EINVAL, MORPH_ENOMEM, MORPH_ECUDA; MORPH_ECAPACITY latched
+ * when there are more blocks than max_boxes. */
+MORPH_API size_t morph_layout_workspace_size(const morph_image *page);
+MORPH_API morph_status morph_layout_boxes(morph_component *boxes, int64_t max_boxes, int64_t *n_boxes,
+                                          int32_t *gaps, const morph_image *page, int coverage_pct,
+                                          void *workspace, size_t workspace_bytes, void *stream);
+
 /* Run-length statistics (section "Other Operations"): histograms of the
  * lengths of the black runs (1-pixels) and of the white runs (maximal gaps
  * of 0-pixels in a row, the ones at either end of the row included; an empty

@@ -104,6 +104,10 @@ def _load():
     lib.morph_rle_transpose_workspace_size.restype = sz
     lib.morph_rle_transpose.argtypes = [img_p, img_p, vp, sz, vp]
     lib.morph_rle_transpose.restype = ci
+    lib.morph_layout_workspace_size.argtypes = [img_p]
+    lib.morph_layout_workspace_size.restype = sz
+    lib.morph_layout_boxes.argtypes = [vp, ctypes.c_int64, vp, i32p, img_p, ci, vp, sz, vp]
+    lib.morph_layout_boxes.restype = ci
     lib.morph_components_workspace_size.argtypes = [img_p]
     lib.morph_components_workspace_size.restype = sz
     lib.morph_rle_components.argtypes = [vp, vp, ctypes.c_int64, vp, img_p, ci, vp, sz, vp]
@@ -483,6 +487,32 @@ def rle_components(src: Rle, connectivity: int = 4, labels: torch.Tensor | None 
                                      max_c, n_components.data_ptr(), ctypes.byref(src.desc()),
                                      int(connectivity), wp, wn, _stream_handle(stream)))
     return labels, stats, n_components
+
+
+def layout_workspace_size(page: Packed) -> int:
+    return int(_lib.morph_layout_workspace_size(ctypes.byref(page.desc())))
+
+
+def layout_boxes(page: Packed, coverage_pct: int = 90, max_boxes: int = 65536,
+                 boxes: torch.Tensor | None = None, n_boxes: torch.Tensor | None = None,
+                 workspace: torch.Tensor | None = None, stream=None):
+    """Layout blocks of a packed page: gap estimates from white run lengths,
+    dilation by the estimated rectangle, bounding boxes of the 8-connected
+    components.  Returns ``(boxes int64[max_boxes, 7], n_boxes int64[1],
+    (gap_h, gap_v))``; columns of ``boxes`` as ``COMPONENT_FIELDS``."""
+    dev = page.words.device
+    if boxes is None:
+        boxes = torch.empty((max(max_boxes, 1), 7), dtype=torch.int64, device=dev)
+    if n_boxes is None:
+        n_boxes = torch.zeros(1, dtype=torch.int64, device=dev)
+    if workspace is None:
+        workspace = torch.empty(max(layout_workspace_size(page), 1), dtype=torch.uint8, device=dev)
+    wp, wn = _ws_args(workspace)
+    gaps = (ctypes.c_int32 * 2)()
+    _check(_lib.morph_layout_boxes(boxes.data_ptr(), int(boxes.shape[0]), n_boxes.data_ptr(), gaps,
+                                   ctypes.byref(page.desc()), int(coverage_pct), wp, wn,
+                                   _stream_handle(stream)))
+    return boxes, n_boxes, (int(gaps[0]), int(gaps[1]))
 
 
 def run_length_hist(src: Rle, black: torch.Tensor | None = None, white: torch.Tensor | None = None,

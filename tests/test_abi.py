@@ -200,3 +200,27 @@ def test_sheared_line_checks(M):
     assert call(nws=need - 1) == M.MORPH_ENOMEM
     assert call(ws=0x900010) == M.MORPH_EINVAL           # not 256-byte aligned
     assert call(s=_img(M, W=100, H=10, words=0x90000 + 8, stride=2)) == M.MORPH_EINVAL  # overlap
+
+
+def test_layout_checks(M):
+    L = M.lib()
+    page = _img(M, W=100, H=10, words=0x10000, stride=2)
+    need = L.morph_layout_workspace_size(ctypes.byref(page))
+    assert need > 0 and need % 256 == 0
+    wide = _img(M, W=70000, H=10, words=0x10000, stride=1100)
+    assert L.morph_layout_workspace_size(ctypes.byref(wide)) == 0
+    gaps = (ctypes.c_int32 * 2)()
+
+    def call(pg=page, boxes=0x50000, max_b=10, n=0x60000, pct=90, ws=0x900000, nws=need):
+        return L.morph_layout_boxes(boxes, max_b, n, gaps, ctypes.byref(pg) if pg else None, pct, ws, nws,
+                                    None)
+    assert call(pg=None) == M.MORPH_EINVAL
+    assert call(pg=wide) == M.MORPH_EINVAL
+    assert call(boxes=None) == M.MORPH_EINVAL
+    assert call(n=None) == M.MORPH_EINVAL
+    assert call(max_b=-1) == M.MORPH_EINVAL
+    assert call(pct=0) == M.MORPH_EINVAL
+    assert call(pct=101) == M.MORPH_EINVAL
+    assert call(ws=None) == M.MORPH_ENOMEM
+    assert call(nws=need - 1) == M.MORPH_ENOMEM
+    assert call(ws=0x900010) == M.MORPH_EINVAL

@@ -428,25 +428,29 @@ __global__ void __launch_bounds__(CC_THREADS) k_cc_label(RleIn in, int32_t *labe
         const int prev_lab = __shfl_up_sync(0xFFFFFFFFu, lab, 1);
         const int prev_y = __shfl_up_sync(0xFFFFFFFFu, y, 1);
         const bool head = lane == 0 || prev_lab != lab || prev_y != y;
-        const int seg = __popc(__ballot_sync(0xFFFFFFFFu, head) & le);
+        const unsigned heads = __ballot_sync(0xFFFFFFFFu, head);
+        const int seg = __popc(heads & le);
         const int len = e - s;
         int area = len;
         int64_t sx = (int64_t)(s + e - 1) * len / 2;
         int x0 = s;
+        bool tail = true;
+        if (heads != 0xFFFFFFFFu) {  // some lanes share a segment: sum it first
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int a_up = __shfl_up_sync(0xFFFFFFFFu, area, off);
-            const int64_t sx_up = __shfl_up_sync(0xFFFFFFFFu, sx, off);
-            const int seg_up = __shfl_up_sync(0xFFFFFFFFu, seg, off);
-            const int x0_up = __shfl_up_sync(0xFFFFFFFFu, x0, off);
-            if (lane >= off && seg_up == seg) {
-                area += a_up;
-                sx += sx_up;
-                x0 = x0_up;  // runs of a line ascend: the segment's first start
+            for (int off = 1; off < 32; off <<= 1) {
+                const int a_up = __shfl_up_sync(0xFFFFFFFFu, area, off);
+                const int64_t sx_up = __shfl_up_sync(0xFFFFFFFFu, sx, off);
+                const int seg_up = __shfl_up_sync(0xFFFFFFFFu, seg, off);
+                const int x0_up = __shfl_up_sync(0xFFFFFFFFu, x0, off);
+                if (lane >= off && seg_up == seg) {
+                    area += a_up;
+                    sx += sx_up;
+                    x0 = x0_up;  // runs of a line ascend: the segment's first start
+                }
             }
+            const int nseg = __shfl_down_sync(0xFFFFFFFFu, seg, 1);
+            tail = lane == 31 || nseg != seg;
         }
-        const int nseg = __shfl_down_sync(0xFFFFFFFFu, seg, 1);
-        const bool tail = lane == 31 || nseg != seg;
         if (!(ok && tail && lab < max_c)) continue;
         const int64_t sy = (int64_t)y * area;
         // find or claim the component's slot (linear probing)

@@ -1,14 +1,16 @@
 // Skewing packed rows (section "Scaling, Skewing, and Rotation": a skew moves
 // every line by its own offset) for morphology with sheared line elements
 // (section "Morphology with Lines at Arbitrary Orientations": skew, erode by
-// an axis-parallel line, skew back).  One thread per output word: the word
-// is a funnel shift of the two source words it straddles, source positions
-// outside the source row take the fill value, bits past the output width
-// are 0.
+// an axis-parallel line, skew back).  One warp per piece of an output row
+// (SHIFT_PIECE words), a lane per output word: the word is a funnel shift
+// of the two source words it straddles, source positions outside the source
+// row take the fill value, bits past the output width are 0.
 #include "morph_internal.cuh"
 
 namespace morph {
 namespace {
+
+constexpr int SHIFT_PIECE = 256;  // output words per warp item (long rows split)
 
 // valid-bit mask of an output word whose bit b reads source position q0 + b:
 // the bits with 0 <= q0 + b < n
@@ -33,15 +35,22 @@ __global__ void __launch_bounds__(256) k_shift_rows(const uint32_t *src, int64_t
                                                     int band, int halo, int sign, uint32_t fill) {
     const int nw_src = (src_bits + 31) / 32;
     const int brows = band + 2 * halo;
-    const int64_t total = (int64_t)rows * nw_dst;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int row = (int)(i / nw_dst), k = (int)(i - (int64_t)row * nw_dst);
+    const int lane = threadIdx.x & 31;
+    const int warps = (int)((gridDim.x * blockDim.x) >> 5);
+    // one warp per piece of SHIFT_PIECE words of an output row, its lanes
+    // over the piece's words
+    const int pieces = (nw_dst + SHIFT_PIECE - 1) / SHIFT_PIECE;
+    const int64_t items = (int64_t)rows * pieces;
+    for (int64_t item = (int64_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); item < items; item += warps) {
+        const int row = (int)(item / pieces);
+        const int k0 = (int)(item - (int64_t)row * pieces) * SHIFT_PIECE;
+        const int k1 = min(nw_dst, k0 + SHIFT_PIECE);
         int srow, a;
         if (sign > 0) {
             const int b = row / brows, y = b * band - halo + (row - b * brows);
             if (y < 0 || y >= H) {
-                dst[(int64_t)row * dstride + k] = fill & word_mask(k, dst_bits);
+                for (int k = k0 + lane; k < k1; k += 32)
+                    dst[(int64_t)row * dstride + k] = fill & word_mask(k, dst_bits);
                 continue;
             }
             srow = y;
@@ -51,15 +60,18 @@ __global__ void __launch_bounds__(256) k_shift_rows(const uint32_t *src, int64_t
             srow = b * brows + halo + (row - b * band);
             a = base[b] - shift[row];
         }
-        const int64_t q0 = 32 * (int64_t)k - a;
-        const int64_t wi = q0 >= 0 ? q0 / 32 : -((-q0 + 31) / 32);  // floor(q0 / 32)
-        const int r = (int)(q0 - 32 * wi);
         const uint32_t *rp = src + (int64_t)srow * sstride;
-        const uint32_t w0 = (wi >= 0 && wi < nw_src) ? rp[wi] : 0u;
-        const uint32_t w1 = (wi + 1 >= 0 && wi + 1 < nw_src) ? rp[wi + 1] : 0u;
-        const uint32_t v = r ? ((w0 >> r) | (w1 << (32 - r))) : w0;
-        const uint32_t m = src_range_mask(q0, src_bits);
-        dst[(int64_t)row * dstride + k] = ((v & m) | (fill & ~m)) & word_mask(k, dst_bits);
+        uint32_t *dp = dst + (int64_t)row * dstride;
+        for (int k = k0 + lane; k < k1; k += 32) {
+            const int64_t q0 = 32 * (int64_t)k - a;
+            const int64_t wi = q0 >> 5;  // floor(q0 / 32): arithmetic shift
+            const int r = (int)(q0 & 31);
+            const uint32_t w0 = (wi >= 0 && wi < nw_src) ? rp[wi] : 0u;
+            const uint32_t w1 = (wi + 1 >= 0 && wi + 1 < nw_src) ? rp[wi + 1] : 0u;
+            const uint32_t v = r ? ((w0 >> r) | (w1 << (32 - r))) : w0;
+            const uint32_t m = src_range_mask(q0, src_bits);
+            dp[k] = ((v & m) | (fill & ~m)) & word_mask(k, dst_bits);
+        }
     }
 }
 
@@ -69,8 +81,8 @@ cudaError_t launch_shift_rows(const uint32_t *src, int64_t sstride, int src_bits
                               int64_t dstride, int dst_bits, int nw_dst, int rows, int H, const int32_t *shift,
                               const int32_t *base, int band, int halo, int sign, uint32_t fill,
                               cudaStream_t s) {
-    const int64_t total = (int64_t)rows * nw_dst;
-    int64_t g = (total + 255) / 256;
+    const int64_t items = (int64_t)rows * ((nw_dst + SHIFT_PIECE - 1) / SHIFT_PIECE);
+    int64_t g = (items + 7) / 8;  // 8 warps per CTA, one piece each
     if (g > 152 * 16) g = 152 * 16;
     if (g < 1) g = 1;
     k_shift_rows<<<(int)g, 256, 0, s>>>(src, sstride, src_bits, dst, dstride, dst_bits, nw_dst, rows, H, shift,

@@ -22,6 +22,7 @@ bounded sample of the same workload on this host's cores.
 workload, a bounded sample per step.
 """
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -335,8 +336,15 @@ def run_serving(M, args):
         n = max(20, int(rate * args.serve_seconds))
         arr = poisson_arrivals(float(rate), n, seed=5000 + rate)
         pages = np.random.default_rng(rate).integers(0, len(pool), size=n)
-        sb = Server(bex, 40e9).run(arr, pages).summary()
-        sp = Server(pex, 40e9).run(arr, pages).summary()
+        # the garbage collector stays off while requests are timed (both
+        # modes alike): its pauses are host noise, not serving latency
+        gc.collect()
+        gc.disable()
+        try:
+            sb = Server(bex, 40e9).run(arr, pages).summary()
+            sp = Server(pex, 40e9).run(arr, pages).summary()
+        finally:
+            gc.enable()
         keep = ("p50_ms", "p99_ms", "sustained_pages_s", "mean_batch", "max_in_flight")
         out[str(rate)] = {"requests": n,
                           "batched": {k: (round(sb[k], 3) if isinstance(sb[k], float) else sb[k]) for k in keep},

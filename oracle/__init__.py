@@ -1,6 +1,7 @@
 """Plain CPU oracle for rectangular binary morphology, run-length coding,
-connected components of RLE images, run-length statistics, transposition
-and sheared line structuring elements.
+connected components of RLE images, run-length statistics, transposition,
+sheared line structuring elements and their skew tables, and the layout
+analysis built from them.
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
@@ -19,6 +20,7 @@ Conventions (all arrays are numpy):
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -85,6 +87,8 @@ def _load():
             lib.oracle_transpose.restype = None
             lib.oracle_sheared_line.argtypes = [u8p, u8p, ci, ci, i32p, ci, ci, ci]
             lib.oracle_sheared_line.restype = None
+            lib.oracle_layout_gap.argtypes = [i64p, ci, ci]
+            lib.oracle_layout_gap.restype = ci
             _lib = lib
     return _lib
 
@@ -443,3 +447,82 @@ def sheared_line(op: str, img, shift, length: int, origin: int, horizontal: bool
         return one(one(a, 1), 0)
     raise ValueError(op)
 
+
+
+def line_table(angle_deg: float, half_length: int, width: int, height: int):
+    """Skew table and line of a line element at an angle (section "Morphology
+    with Lines at Arbitrary Orientations": skew perpendicular to the line by
+    the tangent of its angle from the nearer axis, then an axis-parallel line
+    of about 2 r cos(angle) pixels; the paper fixes neither the rounding nor
+    the axis at exactly 45 degrees).
+
+    Reading: the angle is in degrees counterclockwise from the x axis with
+    image rows growing downwards, reduced to [-90, 90).  A line within 45
+    degrees of the x axis (45 included) runs along the rows: the table has
+    one entry per column, the nearest integer (ties upwards) to x tan(a),
+    and moves column x down.  Any other line runs along the columns: one
+    entry per row, the nearest integer to y tan(90 - a), moving row y right.
+    The line has 2 c + 1 pixels with c = half_length |cos| of that same
+    angle rounded to the nearest integer (ties away from zero), origin c.
+    Double precision, as the C library computes tan and cos.
+
+    Returns ``(shift int32 array, length, origin, horizontal)`` — the
+    arguments of ``sheared_line``."""
+    if half_length < 0 or width < 1 or height < 1 or not math.isfinite(angle_deg):
+        raise ValueError("bad line element")
+    a = math.fmod(float(angle_deg) + 90.0, 180.0)
+    if a < 0.0:
+        a += 180.0
+    a -= 90.0
+    along_rows = -45.0 <= a <= 45.0
+    off = a if along_rows else 90.0 - a
+    rad = off * (math.pi / 180.0)
+    t = math.tan(rad)
+    n = width if along_rows else height
+    shift = np.empty(n, np.int32)
+    for i in range(n):
+        shift[i] = math.floor(i * t + 0.5)
+    v = half_length * abs(math.cos(rad))
+    c = int(math.floor(v + 0.5))  # v >= 0: ties away from zero
+    return shift, 2 * c + 1, c, along_rows
+
+
+# ------------------------------------------------------- layout analysis --
+
+def layout_gap(white, lmax: int, pct: int) -> int:
+    """Gap estimate from a white-run histogram (section "Document Analysis
+    Performance"; the rule is the reading stated in ``oracle_layout_gap``):
+    the smallest L in 1..lmax whose white runs of length <= L are at least
+    pct percent of those of length 1..lmax, 0 if there are none."""
+    if lmax < 1 or not (1 <= pct <= 100):
+        raise ValueError("lmax >= 1 and pct in 1..100")
+    w = np.zeros(lmax + 1, np.int64)
+    src = np.asarray(white, dtype=np.int64)
+    k = min(lmax + 1, src.shape[0])
+    w[:k] = src[:k]
+    return int(_load().oracle_layout_gap(_ptr(w, ctypes.c_int64), int(lmax), int(pct)))
+
+
+def layout_boxes(page, pct: int = 90):
+    """The paper's morphological layout analysis (section "Document Analysis
+    Performance"), composed from the oracle's own steps: white-run histograms
+    along the lines and, through the transpose, along the columns; a gap
+    estimate from each (``layout_gap`` with lmax = 1/16 of the line, at
+    least 1); dilation by a (gap_h + 1) x (gap_v + 1) rectangle with its
+    origin at the centre; the 8-connected components of the result and their
+    records (``rle_component_stats``), numbered in raster order.
+
+    Returns ``((gap_h, gap_v), records int64[n, 7])``."""
+    a = _as_img(page)
+    H, W = a.shape
+    rp, runs = rle_encode(a)
+    _, white_h = run_length_hist(rp, runs, W, H)
+    rpt, runst = rle_encode(transpose(a))
+    _, white_v = run_length_hist(rpt, runst, H, W)
+    gh = layout_gap(white_h, max(W // 16, 1), pct)
+    gv = layout_gap(white_v, max(H // 16, 1), pct)
+    sw, sh = gh + 1, gv + 1
+    d = dilate(a, sw, sh, sw // 2, sh // 2, mode="separable")
+    rpd, runsd = rle_encode(d)
+    labels, n = rle_components(rpd, runsd, H, 8)
+    return (gh, gv), rle_component_stats(labels, n, rpd, runsd, H)

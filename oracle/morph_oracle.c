@@ -469,3 +469,26 @@ EXPORT void oracle_sheared_line(uint8_t *out, const uint8_t *in, int W, int H,
         }
     }
 }
+
+/* ---------------------------------------------------- layout analysis */
+
+/* Section "Document Analysis Performance": the spacing of words and of
+ * lines is estimated from the lengths of the white runs, but the paper does
+ * not give the rule.  Reading: the estimate is the smallest length L in
+ * 1 .. lmax such that the white runs of length at most L make up at least
+ * pct percent of all white runs of length at most lmax (longer gaps —
+ * margins, gutters, blank lines — are left out of both counts); 0 when no
+ * white run has a length in 1 .. lmax.  white[L], L = 0 .. lmax, counts the
+ * white runs of length L.  Integer arithmetic only. */
+EXPORT int oracle_layout_gap(const int64_t *white, int lmax, int pct) {
+    int64_t total = 0;
+    for (int L = 1; L <= lmax; L++) total += white[L];
+    if (total == 0) return 0;
+    int64_t upto = 0;
+    int L = 1;
+    for (;;) {
+        upto += white[L];
+        if (upto * 100 >= (int64_t)pct * total || L == lmax) return L;
+        L++;
+    }
+}

@@ -246,6 +246,27 @@ MORPH_API morph_status morph_sheared_line(int op, const morph_image *dst, const 
                                           int horizontal, void *workspace, size_t workspace_bytes,
                                           void *stream);
 
+/* Skew table and line of a line element at an angle, built as the paper
+ * builds one (section "Morphology with Lines at Arbitrary Orientations":
+ * skew perpendicular to the line by the tangent of the line's angle from its
+ * nearer axis, then an axis-parallel line of about 2 r cos(angle) pixels).
+ * The outputs are the arguments of morph_sheared_line.
+ *   angle_deg: degrees counterclockwise from the x axis, image rows growing
+ *     downwards; any finite value (reduced to a in [-90, 90)).
+ *   Lines with |a| <= 45 run along the rows: *horizontal = 1,
+ *     *n_shift = width, shift[x] = floor(x tan(a) + 1/2) moves column x down.
+ *   Other lines run along the columns: *horizontal = 0, *n_shift = height,
+ *     shift[y] = floor(y tan(90 - a) + 1/2) moves row y right.
+ *   *length = 2 c + 1, *origin = c, c = half_length |cos| of the same angle
+ *     rounded to the nearest integer (ties away from zero).
+ * shift: HOST int32[capacity], written up to *n_shift entries.  Double
+ * precision throughout.  Errors: MORPH_EINVAL (NULL output, half_length < 0,
+ * width or height < 1, a non-finite angle, capacity below the table's
+ * length); nothing is written then. */
+MORPH_API morph_status morph_line_element(double angle_deg, int half_length, int width, int height,
+                                          int32_t *shift, int capacity, int *n_shift, int *length,
+                                          int *origin, int *horizontal);
+
 /* ------------------------------------------------------------- transpose --
  * Section "Efficient Transpose": dst(x, y) = src(y, x).
  * morph_transpose: packed src (W x H) -> packed dst (H x W), either word

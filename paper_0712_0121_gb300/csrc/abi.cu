@@ -1,5 +1,6 @@
 // C ABI entry points of libmorph.so: argument checks, the choice of kernels
 // for each operation and format, workspace layout and the device status latch.
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -9,6 +10,7 @@
 #include <vector>
 
 #include "morph_internal.cuh"
+#include "rect_tile.cuh"
 
 namespace morph {
 
@@ -75,19 +77,6 @@ morph_status check_image(const morph_image *im, const char *name) {
     return fail(MORPH_EINVAL, "%s.fmt %d is not a morph_format", name, im->fmt);
 }
 
-// Clip the rectangle to what can reach inside the image: a window side that
-// sticks out further than W-1 (H-1) pixels covers the same clipped pixels.
-struct Se {
-    int sw, sh, ox, oy;
-};
-Se clip_se(int W, int H, int sw, int sh, int ox, int oy) {
-    int l = ox, r = sw - 1 - ox, u = oy, d = sh - 1 - oy;
-    if (l > W - 1) l = W - 1;
-    if (r > W - 1) r = W - 1;
-    if (u > H - 1) u = H - 1;
-    if (d > H - 1) d = H - 1;
-    return {l + r + 1, u + d + 1, l, u};
-}
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -118,6 +107,19 @@ RleWs rle_ws(int op, int W, int H) {
     return w;
 }
 
+}  // namespace
+
+// Clip the rectangle to what can reach inside the image: a window side that
+// sticks out further than W-1 (H-1) pixels covers the same clipped pixels.
+Se clip_se(int W, int H, int sw, int sh, int ox, int oy) {
+    int l = ox, r = sw - 1 - ox, u = oy, d = sh - 1 - oy;
+    if (l > W - 1) l = W - 1;
+    if (r > W - 1) r = W - 1;
+    if (u > H - 1) u = H - 1;
+    if (d > H - 1) d = H - 1;
+    return {l + r + 1, u + d + 1, l, u};
+}
+
 morph_status check_op_args(int op, const morph_image *dst, const morph_image *src, int se_w,
                            int se_h, int ox, int oy) {
     morph_status st = check_image(src, "src");
@@ -146,6 +148,8 @@ morph_status check_op_args(int op, const morph_image *dst, const morph_image *sr
     return MORPH_OK;
 }
 
+namespace {
+
 // Horizontal reach of one fused launch (register window of 4 words).
 constexpr int MAX_REACH = 128;
 
@@ -172,7 +176,7 @@ struct PackedBuf {
 };
 
 cudaError_t packed_launch(int op, int W, int H, PackedBuf b, Se se, cudaStream_t s) {
-    PackedArgs a;
+    RectArgs a;
     memset(&a, 0, sizeof(a));
     a.src = b.src;
     a.sstride = b.sstride;
@@ -182,8 +186,23 @@ cudaError_t packed_launch(int op, int W, int H, PackedBuf b, Se se, cudaStream_t
     a.H = H;
     a.nw_valid = (W + 31) / 32;
     a.nw_cover = b.nw_cover;
-    if (packed_plan(a, op, se.sw, se.sh, se.ox, se.oy, 0, 0) != 0) return cudaErrorInvalidValue;
-    return launch_packed(a, s);
+    // erosion / dilation: the vertical-first tile; opening / closing, and
+    // windows taller than its van Herk / Gil-Werman rings hold: the tile with
+    // bit-sliced column counters (one stage's ring less in shared memory)
+    if ((op == MORPH_ERODE || op == MORPH_DILATE) && rect_plan(a, op, se.sw, se.sh, se.ox, se.oy, 0, 0, 0, 0) == 0)
+        return launch_rect(a, s);
+    PackedArgs p;
+    memset(&p, 0, sizeof(p));
+    p.src = b.src;
+    p.sstride = b.sstride;
+    p.dst = b.dst;
+    p.dstride = b.dstride;
+    p.W = W;
+    p.H = H;
+    p.nw_valid = (W + 31) / 32;
+    p.nw_cover = b.nw_cover;
+    if (packed_plan(p, op, se.sw, se.sh, se.ox, se.oy, 0, 0) != 0) return cudaErrorInvalidValue;
+    return launch_packed(p, s);
 }
 
 // Erosion (or dilation) by a rectangle whose horizontal reach exceeds one
@@ -820,6 +839,35 @@ morph_status morph_sheared_line(int op, const morph_image *dst, const morph_imag
         if (e == cudaSuccess) e = launch_transpose(XD, nwt, H, W, dw, dstride, cover, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "sheared line launch");
+    return MORPH_OK;
+}
+
+morph_status morph_line_element(double angle_deg, int half_length, int width, int height, int32_t *shift,
+                                int capacity, int *n_shift, int *length, int *origin, int *horizontal) {
+    if (!shift || !n_shift || !length || !origin || !horizontal)
+        return fail(MORPH_EINVAL, "morph_line_element: NULL output");
+    if (half_length < 0 || width < 1 || height < 1 || !std::isfinite(angle_deg))
+        return fail(MORPH_EINVAL, "morph_line_element: half length %d, %d x %d image, angle %g", half_length,
+                    width, height, angle_deg);
+    // reduce to [-90, 90): the same line a half turn away
+    double a = std::fmod(angle_deg + 90.0, 180.0);
+    if (a < 0.0) a += 180.0;
+    a -= 90.0;
+    // within 45 degrees of the x axis the line runs along the rows and the
+    // skew moves columns; otherwise it runs along the columns and moves rows
+    const bool rows = a >= -45.0 && a <= 45.0;
+    const double off = rows ? a : 90.0 - a;  // angle from the nearer axis
+    const double rad = off * (M_PI / 180.0);
+    const double t = std::tan(rad);
+    const int n = rows ? width : height;
+    if (capacity < n)
+        return fail(MORPH_EINVAL, "morph_line_element: the table needs %d entries, capacity %d", n, capacity);
+    for (int i = 0; i < n; ++i) shift[i] = (int32_t)std::floor((double)i * t + 0.5);
+    const int c = (int)std::floor((double)half_length * std::fabs(std::cos(rad)) + 0.5);
+    *n_shift = n;
+    *length = 2 * c + 1;
+    *origin = c;
+    *horizontal = rows ? 1 : 0;
     return MORPH_OK;
 }
 

@@ -45,6 +45,19 @@ __device__ __forceinline__ uint32_t prefix_xor(uint32_t x) {
     return x;
 }
 
+// Argument checks of the rectangle entry points (abi.cu), shared by every
+// entry point that takes an operation, two images and a rectangle.
+struct Se {
+    int sw, sh, ox, oy;
+};
+// The rectangle clipped to what can reach inside a W x H image.
+Se clip_se(int W, int H, int sw, int sh, int ox, int oy);
+// Images valid, same size, both packed or both RLE, not overlapping; op a
+// morph_op; rectangle 1..65535 on each side with the origin inside.  Sets
+// the error message on failure.
+morph_status check_op_args(int op, const morph_image *dst, const morph_image *src, int se_w, int se_h,
+                           int ox, int oy);
+
 // ------------------------------------------------------------- packed ---
 // Parameters of the fused packed tile kernel.  Rows are read and written as
 // 32-bit words (a PACKED64 row is the same little-endian bit string).

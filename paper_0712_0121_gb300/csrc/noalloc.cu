@@ -67,10 +67,6 @@ morph_status reject(morph_status st, const char *fmt, ...) {
     return st;
 }
 
-bool ranges_overlap(const void *a, size_t an, const void *b, size_t bn) {
-    const uintptr_t a0 = (uintptr_t)a, b0 = (uintptr_t)b;
-    return an && bn && a0 < b0 + bn && b0 < a0 + an;
-}
 
 }  // namespace
 }  // namespace morph
@@ -82,47 +78,23 @@ extern "C" morph_status morph_rle_rect_noalloc(int op, const morph_image *dst,
                                                int origin_x, int origin_y, void *stream) {
     if (op != MORPH_ERODE && op != MORPH_DILATE)
         return reject(MORPH_EINVAL, "morph_rle_rect_noalloc supports MORPH_ERODE and MORPH_DILATE only");
-    if (!dst || !src) return reject(MORPH_EINVAL, "dst or src is NULL");
-    if (src->fmt != MORPH_RLE || dst->fmt != MORPH_RLE || src->reserved || dst->reserved)
-        return reject(MORPH_EINVAL, "src and dst must be RLE images");
-    if (src->width < 1 || src->height < 1 || src->width > 65535 || dst->width != src->width ||
-        dst->height != src->height)
-        return reject(MORPH_EINVAL, "bad or different image sizes (%d x %d, %d x %d)", src->width,
-                      src->height, dst->width, dst->height);
+    const morph_status st = check_op_args(op, dst, src, se_w, se_h, origin_x, origin_y);
+    if (st != MORPH_OK) return st;
+    if (src->fmt != MORPH_RLE)
+        return reject(MORPH_EINVAL, "morph_rle_rect_noalloc takes RLE images");
     if (src->height > NOALLOC_MAX_ROWS)
         return reject(MORPH_EINVAL, "image height %d exceeds the %d rows of the fixed scratch of "
                       "morph_rle_rect_noalloc", src->height, NOALLOC_MAX_ROWS);
-    if (!src->row_ptr || !dst->row_ptr || dst->capacity_runs < 0 || src->capacity_runs < 0 ||
-        (dst->capacity_runs > 0 && !dst->runs))
-        return reject(MORPH_EINVAL, "NULL row_ptr or runs, or negative capacity");
-    if ((uintptr_t)src->runs % 4 || (uintptr_t)dst->runs % 4)
-        return reject(MORPH_EINVAL, "runs must be aligned to 4 bytes (one (start, end) pair)");
-    if (se_w < 1 || se_h < 1 || se_w > 65535 || se_h > 65535 || origin_x < 0 || origin_x >= se_w ||
-        origin_y < 0 || origin_y >= se_h)
-        return reject(MORPH_EINVAL, "bad structuring element %d x %d, origin (%d, %d)", se_w, se_h,
-                      origin_x, origin_y);
-    const size_t rp = (size_t)(src->height + 1) * sizeof(int32_t);
-    if (ranges_overlap(dst->row_ptr, rp, src->row_ptr, rp) ||
-        ranges_overlap(dst->runs, (size_t)dst->capacity_runs * 4, src->runs, (size_t)src->capacity_runs * 4) ||
-        ranges_overlap(dst->row_ptr, rp, src->runs, (size_t)src->capacity_runs * 4) ||
-        ranges_overlap(dst->runs, (size_t)dst->capacity_runs * 4, src->row_ptr, rp))
-        return reject(MORPH_EINVAL, "dst overlaps src");
 
     cudaError_t e;
     int32_t *counts = noalloc_scratch(&e);
     if (!counts) return reject(MORPH_ECUDA, "scratch address: %s", cudaGetErrorString(e));
 
-    // clip the rectangle to what can reach inside the image
     const int W = src->width, H = src->height;
-    int l = origin_x, r = se_w - 1 - origin_x, u = origin_y, d = se_h - 1 - origin_y;
-    if (l > W - 1) l = W - 1;
-    if (r > W - 1) r = W - 1;
-    if (u > H - 1) u = H - 1;
-    if (d > H - 1) d = H - 1;
-
+    const Se se = clip_se(W, H, se_w, se_h, origin_x, origin_y);
     const RleIn in{src->row_ptr, src->runs, W, H};
     const RleOut out{dst->row_ptr, dst->runs, dst->capacity_runs, dst->n_runs};
-    e = launch_rle_rect(in, out, op == MORPH_DILATE, l + r + 1, u + d + 1, l, u, counts, nullptr,
+    e = launch_rle_rect(in, out, op == MORPH_DILATE, se.sw, se.sh, se.ox, se.oy, counts, nullptr,
                         device_status_ptr(), (cudaStream_t)stream);
     if (e != cudaSuccess) return reject(MORPH_ECUDA, "RLE morphology launch: %s", cudaGetErrorString(e));
     return MORPH_OK;

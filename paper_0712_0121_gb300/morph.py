@@ -15,7 +15,6 @@ Images:
 from __future__ import annotations
 
 import ctypes
-import math
 import os
 
 import numpy as np
@@ -98,6 +97,9 @@ def _load():
     lib.morph_sheared_line_workspace_size.restype = sz
     lib.morph_sheared_line.argtypes = [ci, img_p, img_p, i32p, ci, ci, ci, ci, vp, sz, vp]
     lib.morph_sheared_line.restype = ci
+    lib.morph_line_element.argtypes = [ctypes.c_double, ci, ci, ci, i32p, ci, ctypes.POINTER(ci),
+                                       ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(ci)]
+    lib.morph_line_element.restype = ci
     lib.morph_transpose.argtypes = [img_p, img_p, vp]
     lib.morph_transpose.restype = ci
     lib.morph_rle_transpose_workspace_size.argtypes = [img_p]
@@ -387,20 +389,16 @@ def rle_to_bitmap(dst: Packed, src: Rle, stream=None) -> None:
 
 def line_element(angle_deg: float, half_length: int, width: int, height: int):
     """Skew table and line of a line element of half length r at an angle
-    (degrees, counterclockwise from the x axis), as the paper builds it: the
-    skew perpendicular to the erosion is tan of the angle from the line's
-    nearer axis, and the axis-parallel line has 2 round(r cos) + 1 pixels.
-    Returns (shift int32 array, length, origin, horizontal)."""
-    a = (float(angle_deg) + 90.0) % 180.0 - 90.0      # [-90, 90)
-    horizontal = abs(a) <= 45.0
-    # image rows grow downwards: a line rising to the right at angle a has
-    # points (x + i, y - i tan a) (along the rows) or (x - j cot a, y + j)
-    off = a if horizontal else 90.0 - a
-    t = math.tan(math.radians(off))
-    n = width if horizontal else height
-    shift = np.floor(np.arange(n) * t + 0.5).astype(np.int32)
-    c = int(round(half_length * abs(math.cos(math.radians(off)))))
-    return shift, 2 * c + 1, c, horizontal
+    (degrees, counterclockwise from the x axis), computed by the library's
+    ``morph_line_element``.  Returns (shift int32 array, length, origin,
+    horizontal), the arguments of ``sheared_line``."""
+    cap = max(int(width), int(height), 1)
+    shift = np.zeros(cap, np.int32)
+    n, L, o, hz = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(_lib.morph_line_element(float(angle_deg), int(half_length), int(width), int(height),
+                                   shift.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), cap,
+                                   ctypes.byref(n), ctypes.byref(L), ctypes.byref(o), ctypes.byref(hz)))
+    return shift[:n.value].copy(), L.value, o.value, bool(hz.value)
 
 
 def sheared_line_workspace_size(op, src: Packed, shift, length: int, horizontal: bool = False) -> int:

@@ -224,3 +224,42 @@ def test_layout_checks(M):
     assert call(ws=None) == M.MORPH_ENOMEM
     assert call(nws=need - 1) == M.MORPH_ENOMEM
     assert call(ws=0x900010) == M.MORPH_EINVAL
+
+
+def test_line_element_through_the_abi_equals_the_oracle_table(M):
+    """morph_line_element (host arithmetic of the library, no GPU) against
+    the oracle's independently written table, whose own pins are exact
+    tables worked out by hand."""
+    import numpy as np
+
+    import oracle
+    angles = [0.0, 45.0, 90.0, 135.0, -20.0, 170.0, 60.0, -75.0, -45.0, 44.999, 45.001, 89.5, -89.5,
+              12.34, 1000.0, -3600.0 + 7.5]
+    for angle in angles:
+        for r, W, H in [(0, 1, 1), (12, 61, 40), (25, 300, 257), (7, 5, 900)]:
+            buf = (ctypes.c_int32 * max(W, H))()
+            n, L, o, hz = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+            st = M.lib().morph_line_element(angle, r, W, H, buf, max(W, H), ctypes.byref(n), ctypes.byref(L),
+                                            ctypes.byref(o), ctypes.byref(hz))
+            assert st == M.MORPH_OK
+            shift, length, origin, horizontal = oracle.line_table(angle, r, W, H)
+            assert (L.value, o.value, bool(hz.value)) == (length, origin, horizontal), (angle, r)
+            assert n.value == shift.shape[0]
+            assert np.array_equal(np.frombuffer(buf, np.int32)[:n.value], shift), (angle, r, W, H)
+            # the binding returns the same table
+            s2, L2, o2, h2 = M.line_element(angle, r, W, H)
+            assert np.array_equal(s2, shift) and (L2, o2, h2) == (length, origin, horizontal)
+
+
+def test_line_element_rejects_bad_arguments(M):
+    buf = (ctypes.c_int32 * 8)()
+    out = [ctypes.c_int() for _ in range(4)]
+    refs = [ctypes.byref(v) for v in out]
+    lib = M.lib()
+    assert lib.morph_line_element(10.0, 3, 8, 8, buf, 8, *refs) == M.MORPH_OK
+    assert lib.morph_line_element(10.0, 3, 9, 8, buf, 8, *refs) == M.MORPH_EINVAL  # capacity
+    assert b"capacity" in lib.morph_last_error()
+    assert lib.morph_line_element(float("nan"), 3, 8, 8, buf, 8, *refs) == M.MORPH_EINVAL
+    assert lib.morph_line_element(10.0, -1, 8, 8, buf, 8, *refs) == M.MORPH_EINVAL
+    assert lib.morph_line_element(10.0, 3, 0, 8, buf, 8, *refs) == M.MORPH_EINVAL
+    assert lib.morph_line_element(10.0, 3, 8, 8, None, 8, *refs) == M.MORPH_EINVAL

@@ -1,8 +1,10 @@
-"""Host logic of the line-element helper (no GPU): the skew table, length
-and orientation that ``morph.line_element`` derives from an angle, checked
-geometrically by dilating one pixel with the oracle — the pixels reached lie
-along the intended line (angle counterclockwise from the x axis, image rows
-growing downwards) within the rounding of the skew."""
+"""Host logic of the line-element entry point (no GPU): the skew table,
+length and orientation that ``morph_line_element`` (through
+``morph.line_element``) derives from an angle, checked geometrically by
+dilating one pixel with the oracle — the pixels reached lie along the
+intended line (angle counterclockwise from the x axis, image rows growing
+downwards) within the rounding of the skew — and equal to the oracle's
+table, whose own pins are exact tables worked out by hand."""
 import math
 
 import numpy as np
@@ -48,3 +50,11 @@ def test_axis_choice_and_lengths(M):
     s, L, o, h = M.line_element(45.0, 12, 50, 40)
     assert h and L == 2 * round(12 * math.cos(math.radians(45))) + 1
     assert s.tolist() == list(range(50))
+
+
+@pytest.mark.parametrize("angle", [-89.0, -60.0, -45.0, -30.0, 0.5, 22.5, 45.0, 67.5, 91.0, 225.0])
+def test_equals_the_oracle_table(M, angle):
+    for r, W, H in [(5, 33, 21), (40, 400, 129)]:
+        s, L, o, h = M.line_element(angle, r, W, H)
+        ts, tL, to, th = oracle.line_table(angle, r, W, H)
+        assert np.array_equal(s, ts) and (L, o, h) == (tL, to, th)

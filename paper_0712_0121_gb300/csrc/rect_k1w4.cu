@@ -1,0 +1,6 @@
+// Packed rectangle tile variants with 1 stage(s) and 4 words per thread.
+#include "rect_kernels.cuh"
+
+namespace morph {
+cudaError_t launch_rect_1_4(const RectArgs &a, cudaStream_t s) { return rect_launch_nw<1, 4>(a, s); }
+}  // namespace morph

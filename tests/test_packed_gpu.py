@@ -101,3 +101,21 @@ def test_config3_full_page(kind):
     img, _ = synth.config3_page(kind)
     for op, sw, sh in (("dilate", 101, 1), ("dilate", 1, 61), ("open", 5, 5)):
         check(op, img, sw, sh, sw // 2, sh // 2, mode="separable")
+
+
+def test_vertical_windows_of_every_height_class():
+    """Window heights on both sides of the register-window / van Herk-Gil-
+    Werman switch, block boundaries that do not line up with the row chunks,
+    and heights past the shared-memory limit of the van Herk rings."""
+    img = synth.random_bits((613, 170), 31, 0.85)
+    for op in OPS:
+        for sh in (2, 4, 5, 8, 9, 16, 17, 33, 64, 65, 99, 150, 250):
+            for oy in sorted({0, sh // 2, sh - 1}):
+                check(op, img, 3, sh, 1, oy, mode="separable")
+
+
+def test_rows_wider_than_one_cta_split_into_strips():
+    img = synth.random_bits((7, 70001), 12, 0.9)
+    for op in OPS:
+        for sw, sh, ox, oy in [(3, 3, 1, 1), (129, 4, 64, 2), (40, 7, 3, 6), (1, 5, 0, 2)]:
+            check(op, img, sw, sh, ox, oy, mode="separable")

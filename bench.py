@@ -256,6 +256,145 @@ def time_launches(fn, steps, stream):
     return times
 
 
+# Rectangles of the letter-page and 600-dpi workloads, timed one by one.
+PER_OP_SES = [(3, 3), (5, 5), (7, 7), (15, 15), (31, 31), (51, 51), (1, 51), (51, 1), (101, 1), (1, 61)]
+DENSITY_KINDS = ("blank", "text", "halftone", "noise")
+DENSITY_OPS = (("dilate", 101, 1), ("dilate", 1, 61), ("open", 5, 5))
+
+
+def median_ms(fn, reps, stream):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    return statistics.median(time_launches(fn, reps, stream))
+
+
+def run_per_op(M, dev_in, peak, stream, reps):
+    """Each rectangle of the letter-page and 600-dpi workloads alone, erode /
+    dilate / open / close on the packed path, over the B resident pages seen
+    as one 2550 x (B * 3300) image (more than L2; windows cross the page
+    seams, the same work per pixel).  Algorithmic bytes: one read and one
+    write of the bitmap (2 bits per pixel)."""
+    import torch
+    B = dev_in.shape[0]
+    stack = M.Packed(dev_in.view(B * H, NW), W)
+    dst = M.Packed.empty(W, B * H, 64)
+    page_bytes = B * H * NW * 8
+    out = []
+    for (sw, sh) in PER_OP_SES:
+        row = {"se": "%dx%d" % (sw, sh)}
+        for op in ("erode", "dilate", "open", "close"):
+            ws = torch.empty(max(1, M.workspace_size(op, dst, stack, sw, sh)), dtype=torch.uint8, device="cuda")
+            ms = median_ms(lambda: M.morph_rect(op, dst, stack, sw, sh, workspace=ws), reps, stream)
+            gbs = 2 * page_bytes / (ms * 1e-3) / 1e9
+            row[op] = {"ms": round(ms, 4), "gpix_s": round(W * B * H / (ms * 1e-3) / 1e9, 1),
+                       "alg_gb_s": round(gbs, 1), "frac": round(gbs / peak, 3)}
+        out.append(row)
+    st = M.sync_status()
+    if st != M.MORPH_OK:
+        raise RuntimeError("device status %d after the per-op table" % st)
+    del dst
+    torch.cuda.empty_cache()
+    return out
+
+
+def rle_bytes(W_, H_, runs):
+    return 4 * runs + 4 * (H_ + 1)
+
+
+def run_density_sweep(M, peak, stream, reps, copies):
+    """600-dpi pages (5100 x 6600) of four kinds — near-blank 0.5 %, text 8 %,
+    halftone 45 %, salt-and-pepper 5 % — each stacked `copies` times into one
+    tall image (distinct memory, more than L2).  For each op: the packed path,
+    and the RLE path with runs in and out (bitmap -> runs and runs -> bitmap
+    timed on their own).  Algorithmic bytes: packed 2 bits per pixel; RLE op 4
+    bytes per run in and out plus the row offsets."""
+    import torch
+    from paper_0712_0121_gb300 import synth
+    Wd, Hd = 5100, 6600
+    nwd = (Wd + 63) // 64
+    rows = Hd * copies
+    out = []
+    for kind in DENSITY_KINDS:
+        img, ink = synth.config3_page(kind)
+        one = M.pack(img, 64).words
+        stack_t = one.repeat(copies, 1)
+        stack = M.Packed(stack_t, Wd)
+        dst = M.Packed.empty(Wd, rows, 64)
+        cap = rows * (Wd // 2 + 1)
+        a, b = M.Rle.empty(Wd, rows, cap), M.Rle.empty(Wd, rows, cap)
+        cws = torch.empty(M.convert_workspace_size(rows), dtype=torch.uint8, device="cuda")
+        bmp_bytes = rows * nwd * 8
+        t_enc = median_ms(lambda: M.rle_from_bitmap(a, stack, cws), reps, stream)
+        runs_in = int(a.n_runs.item())
+        t_dec = median_ms(lambda: M.rle_to_bitmap(dst, a), reps, stream)
+        enc_b = bmp_bytes + rle_bytes(Wd, rows, runs_in)
+        rec = {"kind": kind, "ink": round(float(ink), 4), "runs_per_row": round(runs_in / rows, 1),
+               "to_rle": {"ms": round(t_enc, 4), "gpix_s": round(Wd * rows / (t_enc * 1e-3) / 1e9, 1),
+                          "alg_gb_s": round(enc_b / (t_enc * 1e-3) / 1e9, 1),
+                          "frac": round(enc_b / (t_enc * 1e-3) / 1e9 / peak, 3)},
+               "to_bitmap": {"ms": round(t_dec, 4), "gpix_s": round(Wd * rows / (t_dec * 1e-3) / 1e9, 1),
+                             "alg_gb_s": round(enc_b / (t_dec * 1e-3) / 1e9, 1),
+                             "frac": round(enc_b / (t_dec * 1e-3) / 1e9 / peak, 3)},
+               "ops": []}
+        for op, sw, sh in DENSITY_OPS:
+            pws = torch.empty(max(1, M.workspace_size(op, dst, stack, sw, sh)), dtype=torch.uint8, device="cuda")
+            t_p = median_ms(lambda: M.morph_rect(op, dst, stack, sw, sh, workspace=pws), reps, stream)
+            rws = torch.empty(max(1, M.workspace_size(op, b, a, sw, sh)), dtype=torch.uint8, device="cuda")
+            t_r = median_ms(lambda: M.morph_rect(op, b, a, sw, sh, workspace=rws), reps, stream)
+            runs_out = int(b.n_runs.item())
+            pb = 2 * bmp_bytes
+            rb = rle_bytes(Wd, rows, runs_in) + rle_bytes(Wd, rows, runs_out)
+            rec["ops"].append({
+                "op": "%s %dx%d" % (op, sw, sh),
+                "packed": {"ms": round(t_p, 4), "gpix_s": round(Wd * rows / (t_p * 1e-3) / 1e9, 1),
+                           "frac": round(pb / (t_p * 1e-3) / 1e9 / peak, 3)},
+                "rle": {"ms": round(t_r, 4), "gpix_s": round(Wd * rows / (t_r * 1e-3) / 1e9, 1),
+                        "alg_gb_s": round(rb / (t_r * 1e-3) / 1e9, 1),
+                        "frac": round(rb / (t_r * 1e-3) / 1e9 / peak, 3), "runs_out_per_row": round(runs_out / rows, 1),
+                        "with_conversions_gpix_s": round(Wd * rows / ((t_r + t_enc + t_dec) * 1e-3) / 1e9, 1)},
+            })
+            del pws, rws
+        st = M.sync_status()
+        if st != M.MORPH_OK:
+            raise RuntimeError("device status %d in the density sweep (%s)" % (st, kind))
+        out.append(rec)
+        del stack_t, stack, dst, a, b, cws
+        torch.cuda.empty_cache()
+    return {"pages": "one seeded page per kind, stacked %d times (%d rows, %.0f MB packed)"
+                     % (copies, rows, rows * nwd * 8 / 1e6), "results": out}
+
+
+def run_config1(M, stream, reps):
+    """512 x 512 text page (packed u32 rows): erode / dilate by 3x3, 11x1 and
+    1x11 on the packed and RLE paths, and the RLE round trip.  One page is
+    32 KB and stays in L2: these are single-launch latencies."""
+    import torch
+    from paper_0712_0121_gb300 import synth
+    img, ink = synth.config1_page()
+    Hc, Wc = img.shape
+    src = M.pack(img, 32)
+    dst = M.Packed.empty(Wc, Hc, 32)
+    cap = Hc * (Wc // 2 + 1)
+    a, b = M.Rle.empty(Wc, Hc, cap), M.Rle.empty(Wc, Hc, cap)
+    cws = torch.empty(M.convert_workspace_size(Hc), dtype=torch.uint8, device="cuda")
+    rec = {"ink": round(float(ink), 4), "ops": []}
+    t_enc = median_ms(lambda: M.rle_from_bitmap(a, src, cws), reps, stream)
+    t_dec = median_ms(lambda: M.rle_to_bitmap(dst, a), reps, stream)
+    rec["to_rle_us"], rec["to_bitmap_us"] = round(t_enc * 1e3, 2), round(t_dec * 1e3, 2)
+    for op in ("erode", "dilate"):
+        for sw, sh in ((3, 3), (11, 1), (1, 11)):
+            t_p = median_ms(lambda: M.morph_rect(op, dst, src, sw, sh), reps, stream)
+            rws = torch.empty(max(1, M.workspace_size(op, b, a, sw, sh)), dtype=torch.uint8, device="cuda")
+            t_r = median_ms(lambda: M.morph_rect(op, b, a, sw, sh, workspace=rws), reps, stream)
+            rec["ops"].append({"op": "%s %dx%d" % (op, sw, sh), "packed_us": round(t_p * 1e3, 2),
+                               "rle_us": round(t_r * 1e3, 2)})
+    st = M.sync_status()
+    if st != M.MORPH_OK:
+        raise RuntimeError("device status %d in config 1" % st)
+    return rec
+
+
 def run_uneven_batch(M, args, stream):
     """Uneven batch: seeded pages of four sizes, ink density U(1,30) %, each
     with its own rectangle and op; per-page path and band from the autotuner;
@@ -702,6 +841,18 @@ def run_ours(args):
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
 
+    # each rectangle alone, the 600-dpi density sweep and the 512 x 512
+    # config, timed standalone (after the batch numbers, before the e2e run)
+    tables = {}
+    if not args.no_tables:
+        tables["per_op"] = {"image": "the %d resident pages as one 2550 x %d image (%.0f MB packed, > L2)"
+                                     % (B, B * H, B * H * NW * 8 / 1e6),
+                            "results": run_per_op(M, dev_in, peak, stream, args.table_reps)}
+        tables["density_sweep"] = run_density_sweep(M, peak, stream, args.table_reps, args.density_copies)
+        tables["config1"] = run_config1(M, stream, max(10, args.table_reps))
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+
     # end to end through the same API with host buffers
     host_in = torch.empty((B, H, NW), dtype=torch.int64, pin_memory=True)
     host_in.copy_(dev_in)
@@ -777,7 +928,8 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64 rows, 32-bit word lanes, exact bitwise",
         "data": "synthetic (seeded document pages; UW3 scans are not available)",
         "config": {"workload": WORKLOAD, "pages_per_gpu": B, "page_ops_per_step": n_jobs,
                    "parallelism": "pages sharded across GPUs, no collective" if world > 1 else "1 GPU",
@@ -799,6 +951,7 @@ def run_ours(args):
         "clocks": clocks,
         "generation_s": round(t_gen, 2),
     }
+    line.update(tables)
     if not args.no_batch:
         line["uneven_batch"] = run_uneven_batch(M, args, stream)
     if not args.no_serve:
@@ -808,6 +961,9 @@ def run_ours(args):
         pix, dt, desc = oracle_sample(pages[:2], args.cpu_seconds, cores)
         line["cpu_baseline"] = {"value": round(pix / dt / 1e9, 5), "unit": UNIT, "cores": cores,
                                 "kind": "oracle", "sample": desc + ", %.1f s" % dt}
+        pix1, dt1, desc1 = oracle_sample(pages[:1], args.cpu_seconds / 2, 1)
+        line["cpu_baseline_1core"] = {"value": round(pix1 / dt1 / 1e9, 5), "unit": UNIT, "cores": 1,
+                                      "kind": "oracle", "sample": desc1 + ", %.1f s" % dt1}
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -857,6 +1013,11 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the uneven-batch section")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
     ap.add_argument("--batch-pages", type=int, default=256)
+    ap.add_argument("--no-tables", action="store_true",
+                    help="skip the per-rectangle, density-sweep and 512x512 tables")
+    ap.add_argument("--table-reps", type=int, default=5)
+    ap.add_argument("--density-copies", type=int, default=48,
+                    help="copies of each 5100x6600 page in the density-sweep stack (48: 203 MB)")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--tune-cache", default=os.path.join("/tmp", "morph_tune_cache.json"))
     ap.add_argument("--probe", choices=["packed", "rle", "mask", "cc", "xpose", "line", "layout"], default=None,

@@ -189,8 +189,7 @@ cudaError_t packed_launch(int op, int W, int H, PackedBuf b, Se se, cudaStream_t
     // erosion / dilation: the vertical-first tile; opening / closing, and
     // windows taller than its van Herk / Gil-Werman rings hold: the tile with
     // bit-sliced column counters (one stage's ring less in shared memory)
-    if ((op == MORPH_ERODE || op == MORPH_DILATE) && rect_plan(a, op, se.sw, se.sh, se.ox, se.oy, 0, 0, 0, 0) == 0)
-        return launch_rect(a, s);
+    if (rect_plan(a, op, se.sw, se.sh, se.ox, se.oy, 0, 0, 0, 0) == 0) return launch_rect(a, s);
     PackedArgs p;
     memset(&p, 0, sizeof(p));
     p.src = b.src;

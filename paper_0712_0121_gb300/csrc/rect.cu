@@ -20,18 +20,25 @@ int round_up(int v, int m) { return (v + m - 1) / m * m; }
 constexpr int RECT_MAX_GROUPS = 16;
 
 // Optional override of the tiling for tuning runs: MORPH_RECT_TILING =
-// "nwt,threads,band,prefetch_rows" (0 keeps the default of a field; the
-// L2 row prefetch is off by default).  Read once.
+// "nwt,threads,band,prefetch_rows,vmode" (0 keeps the default of the first
+// four fields, -1 of the last; the L2 row prefetch is off by default).  Read
+// once.
 struct TilingOverride {
-    int nwt = 0, threads = 0, band = 0, pf = -1;
+    int nwt = 0, threads = 0, band = 0, pf = -1, vmode = -1;
     TilingOverride() {
         const char *e = getenv("MORPH_RECT_TILING");
-        if (e) sscanf(e, "%d,%d,%d,%d", &nwt, &threads, &band, &pf);
+        if (e) sscanf(e, "%d,%d,%d,%d,%d", &nwt, &threads, &band, &pf, &vmode);
     }
 };
 const TilingOverride &tiling_override() {
     static const TilingOverride t;
     return t;
+}
+
+// Horizontal tasks per thread and chunk for the current groups.
+int task_count(const RectArgs &a) {
+    const int total = rect_rb(a.nst) * a.groups * a.tph;
+    return (total + a.threads - 1) / a.threads;
 }
 
 void set_band(RectArgs &a, int band) {
@@ -43,6 +50,7 @@ void set_band(RectArgs &a, int band) {
     if (a.groups * band > hcap) a.groups = (hcap + band - 1) / band;
     if (a.groups < 1) a.groups = 1;
     a.band = band;
+    a.ktasks = task_count(a);
 }
 
 // Fill the tiling for nwt words per thread and `threads` threads per CTA.
@@ -68,8 +76,12 @@ void tile(RectArgs &a, int nwt, int threads) {
         a.nstrips = (cover + a.strip_words - 1) / a.strip_words;
     }
     a.pad = round_up(a.halo > 0 ? a.halo : 1, 4);
-    a.slot_words = round_up(2 * a.pad + a.tpr * nwt, 4);
+    // a row of the exchange slot holds whole horizontal tasks of RECT_NWH words
+    a.row_words = round_up(a.tpr * nwt, RECT_NWH);
+    a.tph = a.row_words / RECT_NWH;
+    a.slot_words = 2 * a.pad + a.row_words;
 }
+
 
 }  // namespace
 
@@ -107,22 +119,32 @@ int rect_plan(RectArgs &a, int op, int sw, int sh, int ox, int oy, int band_hint
         a.halo = hw <= 1 ? 1 : (hw <= 2 ? 2 : 4);
     }
     a.vmode = sh == 1 ? RV_NONE : (sh <= 3 ? RV_W3 : RV_VHGW);
-
     const TilingOverride &ov = tiling_override();
+    const bool force_v = ov.vmode >= 0 && sh >= 4 && (ov.vmode == RV_VHGW || (ov.vmode == RV_CNT && sh <= RECT_CNT_SH));
+    if (force_v) a.vmode = ov.vmode;
     if (!nwt_hint) nwt_hint = ov.nwt;
     if (!threads_hint) threads_hint = ov.threads;
     if (!band_hint) band_hint = ov.band;
     if (!smem_budget) smem_budget = 110 * 1024;
     // words per thread and CTA size: the first candidate whose shared
     // memory (exchange buffers, van Herk / Gil-Werman rings of sh rows)
-    // fits the budget, so that two CTAs stay resident per SM
+    // fits the budget, so that two CTAs stay resident per SM.  Two stages
+    // whose rings do not fit with 256 threads keep their per-column state
+    // in registers instead (counters, two words per thread: four would
+    // spill).
     const int cand[4][2] = {{4, 256}, {2, 256}, {4, 128}, {2, 128}};
+    const int ncand = (a.nst == 2 && a.vmode == RV_VHGW && !force_v && sh <= RECT_CNT_SH) ? 2 : 4;
     bool done = false;
-    for (int i = 0; i < 4 && !done; ++i) {
+    for (int i = 0; i < ncand && !done; ++i) {
         const int nwt = nwt_hint ? nwt_hint : cand[i][0];
         const int thr = threads_hint ? threads_hint : cand[i][1];
         tile(a, nwt, thr);
         if (rect_smem_words(a) * 4 <= smem_budget || (nwt_hint && threads_hint)) done = true;
+    }
+    if (!done && ncand == 2) {
+        a.vmode = RV_CNT;
+        tile(a, nwt_hint ? nwt_hint : 2, threads_hint ? threads_hint : 256);
+        done = true;
     }
     if (!done) tile(a, 2, 128);
     // windows too tall for the rings of even the smallest tiling: the caller
@@ -144,6 +166,15 @@ int rect_plan(RectArgs &a, int op, int sw, int sh, int ox, int oy, int band_hint
     if (a.nstrips == 1 && (uintptr_t)a.src % 16 == 0 && a.sstride % 4 == 0) {
         a.pf_bytes = (uint32_t)(a.nw_valid * 4) & ~15u;
         if (a.pf_bytes) a.pf_rows = ov.pf > 0 ? ov.pf : 0;  // measured slower on by default
+    }
+    a.nw_full = a.W / 32;
+    a.vec16 = ((uintptr_t)a.dst % 16 == 0) && (a.dstride % 4 == 0);
+    // the horizontal tasks of a chunk must fit the threads' task slots (the
+    // most groups a launch may give the CTA)
+    {
+        RectArgs t = a;
+        t.groups = t.threads / t.tpr;
+        if (task_count(t) > RECT_KT) return -1;
     }
     const int vb = a.nwt * 4;
     a.vec = ((uintptr_t)a.src % vb == 0) && ((uintptr_t)a.dst % vb == 0) && (a.sstride % a.nwt == 0) &&

@@ -74,6 +74,7 @@ cudaError_t rect_launch_nw(const RectArgs &a, cudaStream_t s) {
     switch (a.vmode) {
     case RV_NONE: return rect_launch_h<NST, NWT, RV_NONE>(a, s);
     case RV_W3: return rect_launch_h<NST, NWT, RV_W3>(a, s);
+    case RV_CNT: return rect_launch_h<NST, NWT, RV_CNT>(a, s);
     default: return rect_launch_h<NST, NWT, RV_VHGW>(a, s);
     }
 }

@@ -14,7 +14,11 @@
 //    no exchange between threads:
 //      sh == 1      nothing;
 //      sh <= 3      the AND of a register window of the last rows;
-//      sh >= 4      van Herk / Gil-Werman: rows are taken in blocks of sh;
+//      sh >= 4      van Herk / Gil-Werman (below), or, where its rings would
+//                   take too much shared memory, bit-sliced counters of
+//                   consecutive 1-rows in registers (6 planes, about 20
+//                   logic operations per word);
+//                   van Herk / Gil-Werman: rows are taken in blocks of sh;
 //                   g = prefix AND within the current block (one AND per
 //                   row), s = suffix AND within the previous block (computed
 //                   once per block by a backward sweep over that block's rows,
@@ -48,11 +52,12 @@
 
 #include <type_traits>
 
+#include "counters.cuh"
 #include "morph_internal.cuh"
 
 namespace morph {
 
-enum RectVMode { RV_NONE = 0, RV_W3 = 1, RV_VHGW = 2 };
+enum RectVMode { RV_NONE = 0, RV_W3 = 1, RV_VHGW = 2, RV_CNT = 3 };
 enum RectHMode { RH_NONE = 0, RH_D1 = 1, RH_D2 = 2, RH_LOG = 3 };
 
 struct RectArgs {
@@ -77,16 +82,27 @@ struct RectArgs {
     int band;             // output rows per group
     int strip_words, halo_words, nstrips;
     int pad;              // all-ones words on each side of an exchange slot
-    int slot_words;       // exchange slot: pad + tpr * nwt + pad
+    int slot_words;       // exchange slot: pad + row_words + pad
     int vec;              // aligned bases and strides: vector loads / stores
     int vec_rows;         // vec, and every thread's words lie inside the rows
     int vmode, hmode, halo;  // kernel variant (must match the template)
     int band_auto;        // band chosen at launch from the resident CTAs
+    int row_words;        // words of a row in an exchange slot: tpr * nwt rounded up to RECT_NWH
+    int tph;              // horizontal tasks per row: row_words / RECT_NWH
+    int ktasks;           // horizontal tasks per thread and chunk (at most RECT_KT)
+    int nw_full;          // words holding 32 pixels: W / 32
+    int vec16;            // dst 16-byte aligned and dstride a multiple of 4 words
     int pf_rows;          // rows between a row's L2 prefetch and its use (0: none)
     uint32_t pf_bytes;    // bytes prefetched per row (a multiple of 16)
 };
 
-constexpr int RECT_RB = 8;  // rows per chunk (one barrier per chunk)
+constexpr int RECT_RB = 8;  // bands are whole multiples of this many rows
+// Rows per chunk (one barrier per chunk): 8, or 4 for two stages, whose four
+// exchange buffers would otherwise crowd out the CTAs of an SM.
+__host__ __device__ constexpr int rect_rb(int nst) { return nst == 2 ? 4 : 8; }
+constexpr int RECT_CNT_SH = 63;  // tallest window of the counter mode (6 bit planes)
+constexpr int RECT_NWH = 8;      // words of one horizontal-pass task
+constexpr int RECT_KT = 8;       // horizontal tasks per thread and chunk, at most
 constexpr size_t RECT_SMEM_MAX = 200 * 1024;  // shared memory of one tile at most
 
 template <int NWT>
@@ -115,6 +131,24 @@ struct RectVec<4> {
         x[1] = v.y;
         x[2] = v.z;
         x[3] = v.w;
+    }
+};
+
+template <>
+struct RectVec<8> {
+    struct V {
+        uint4 a, b;
+    };
+    __device__ static V ld(const uint32_t *p) {
+        return V{*reinterpret_cast<const uint4 *>(p), *reinterpret_cast<const uint4 *>(p + 4)};
+    }
+    __device__ static void st(uint32_t *p, const uint32_t (&x)[8]) {
+        *reinterpret_cast<uint4 *>(p) = make_uint4(x[0], x[1], x[2], x[3]);
+        *reinterpret_cast<uint4 *>(p + 4) = make_uint4(x[4], x[5], x[6], x[7]);
+    }
+    __device__ static void get(const V &v, uint32_t (&x)[8]) {
+        x[0] = v.a.x; x[1] = v.a.y; x[2] = v.a.z; x[3] = v.a.w;
+        x[4] = v.b.x; x[5] = v.b.y; x[6] = v.b.z; x[7] = v.b.w;
     }
 };
 
@@ -260,6 +294,9 @@ struct RectV {
     uint32_t *ring;    // VHGW: this thread's column of the ring, entries rstride words apart
     uint32_t *rp;      // VHGW: entry j
     int rstride;
+    ColCounter<6> cnt[NWT];  // CNT: run counters
+    uint32_t eqm[6];         // CNT: per plane, ones where that bit of sh is 0
+    int K;                   // CNT: bit length of sh
 
     __device__ __forceinline__ void init(uint32_t *ring_base, int tid, int threads, int sh) {
 #pragma unroll
@@ -268,6 +305,14 @@ struct RectV {
             p2[t] = ONES;
         }
         keep2 = sh == 3 ? 0u : ONES;
+        if constexpr (VM == RV_CNT) {
+#pragma unroll
+            for (int t = 0; t < NWT; ++t) cnt[t].reset();
+            K = 0;
+            for (int v = sh; v; v >>= 1) ++K;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) eqm[k] = ((sh >> k) & 1) ? 0u : ONES;
+        }
         j = 0;
         ring = ring_base + tid * NWT;
         rstride = threads * NWT;
@@ -295,6 +340,9 @@ struct RectV {
                 p2[t] = g[t] | keep2;
                 g[t] = in[t];
             }
+        } else if constexpr (VM == RV_CNT) {
+#pragma unroll
+            for (int t = 0; t < NWT; ++t) out[t] = cnt[t].push(in[t], K, eqm);
         } else {
             using RV = RectVec<NWT>;
             uint32_t s[NWT];
@@ -309,17 +357,18 @@ struct RectV {
             if (++j == sh) {
                 // suffix ANDs of the block just completed, in place; entry 0
                 // is never read (the window starting there is the full
-                // block).  Entries are read in groups of 4 before any of them
+                // block).  Entries are read in small groups before any of them
                 // is written back, so that the loads overlap.
                 uint32_t acc[NWT];
                 RV::get(RV::ld(ring + (sh - 1) * rstride), acc);
-                for (int q0 = sh - 2; q0 >= 1; q0 -= 4) {
-                    uint32_t x[4][NWT];
+                constexpr int BB = NWT >= 4 ? 2 : 4;  // entries per group (registers)
+                for (int q0 = sh - 2; q0 >= 1; q0 -= BB) {
+                    uint32_t x[BB][NWT];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e)
+                    for (int e = 0; e < BB; ++e)
                         if (q0 - e >= 1) RV::get(RV::ld(ring + (q0 - e) * rstride), x[e]);
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
+                    for (int e = 0; e < BB; ++e) {
                         if (q0 - e >= 1) {
 #pragma unroll
                             for (int t = 0; t < NWT; ++t) acc[t] &= x[e][t];
@@ -336,23 +385,49 @@ struct RectV {
     }
 };
 
-// Shared memory of the tile in u32 words: per stage, two exchange buffers
-// (when there is a horizontal pass) and the van Herk / Gil-Werman ring of
-// sh + 1 entries per thread.
+// Shared memory of the tile in u32 words.  Exchange buffers (when there is a
+// horizontal pass): one set for one stage; for two stages three sets — the
+// stage-1 vertical result, the stage-1 horizontal result handed back to the
+// stage-2 vertical pass, and the stage-2 vertical result.  A set is two
+// chunks of rows, a row slot per group.  Then the van Herk / Gil-Werman ring
+// of sh + 1 entries per thread and stage.
 __host__ __device__ inline size_t rect_xbuf_words(const RectArgs &a) {
-    return (size_t)2 * RECT_RB * a.groups * a.slot_words;
+    return (size_t)2 * rect_rb(a.nst) * a.groups * a.slot_words;
+}
+__host__ __device__ inline int rect_xsets(const RectArgs &a) {
+    return a.hmode == RH_NONE ? 0 : (a.nst == 2 ? 3 : 1);
 }
 __host__ __device__ inline size_t rect_ring_words(const RectArgs &a) {
     return a.vmode == RV_VHGW ? (size_t)(a.sh + 1) * a.threads * a.nwt : 0;
 }
 __host__ __device__ inline size_t rect_smem_words(const RectArgs &a) {
-    const size_t x = a.hmode == RH_NONE ? 0 : rect_xbuf_words(a);
-    return (size_t)a.nst * (x + rect_ring_words(a));
+    return (size_t)rect_xsets(a) * rect_xbuf_words(a) + (size_t)a.nst * rect_ring_words(a);
 }
+
+// Horizontal-pass tasks: every chunk of RB rows splits into RB x groups x
+// tph tasks of RECT_NWH words of one row (task t: row t / (groups tph),
+// group, segment).  A thread takes tasks tid, tid + threads, ... in every
+// chunk; the decomposition of its first task and of the stride between its
+// tasks are worked out once, so the loop only adds and carries.
+struct RectTasks {
+    int total;          // tasks per chunk
+    int i0, g0, s0;     // row, group, segment of task tid
+    int di, dg, ds;     // the same of the stride `threads`
+    __device__ __forceinline__ void init(int tid, int threads, int rb, int groups, int tph) {
+        const int per_row = groups * tph;
+        total = rb * per_row;
+        i0 = tid / per_row;
+        g0 = (tid - i0 * per_row) / tph;
+        s0 = tid - i0 * per_row - g0 * tph;
+        di = threads / per_row;
+        dg = (threads - di * per_row) / tph;
+        ds = threads - di * per_row - dg * tph;
+    }
+};
 
 template <int NST, int NWT, int VM, int HM, int HALO>
 __device__ __forceinline__ void rect_tile(const RectArgs &a, int bx, int by, uint32_t *sm) {
-    constexpr int RB = RECT_RB;
+    constexpr int RB = rect_rb(NST);
     constexpr bool XCH = HM != RH_NONE;  // rows exchanged between threads
     using RV = RectVec<NWT>;
     // a plan made for another variant or CTA size must not run this body
@@ -366,6 +441,7 @@ __device__ __forceinline__ void rect_tile(const RectArgs &a, int bx, int by, uin
     const int gg = act ? g : 0;
     const int strip0 = by * a.strip_words;
     const int w0 = strip0 - a.halo_words + lt * NWT;
+    const int strip_end = strip0 + a.strip_words < a.nw_cover ? strip0 + a.strip_words : a.nw_cover;
     const int Y0 = (bx * groups + gg) * band;
     // Each stage's vertical pass lags sh - 1 rows behind its input; the lag
     // is rounded up to whole chunks (the extra rows are more warm-up), so
@@ -406,10 +482,12 @@ __device__ __forceinline__ void rect_tile(const RectArgs &a, int bx, int by, uin
     const bool pf_lead = act && lt == 0 && a.pf_rows > 0;
     const uint32_t inm_in = a.inv_in ? ONES : 0u, inm_out = a.inv_out ? ONES : 0u;
 
-    // shared memory: [stage 1 exchange][stage 2 exchange][stage 1 ring][stage 2 ring]
+    // shared memory: exchange sets (the stage-1 vertical result; for two
+    // stages also the stage-1 horizontal result and the stage-2 vertical
+    // result), then the rings
     const size_t xw = XCH ? rect_xbuf_words(a) : 0;
-    uint32_t *X1 = sm, *X2 = sm + xw;
-    uint32_t *ring_base = sm + NST * xw;
+    uint32_t *X1 = sm, *Y1 = sm + xw, *X2 = sm + 2 * xw;
+    uint32_t *ring_base = sm + rect_xsets(a) * xw;
     const int row_words = groups * a.slot_words;  // between rows of a chunk
     const int buf_words = RB * row_words;         // between the two buffers
     const int own_off = gg * a.slot_words + a.pad + lt * NWT;
@@ -422,7 +500,7 @@ __device__ __forceinline__ void rect_tile(const RectArgs &a, int bx, int by, uin
         // every word of an exchange slot outside the row (the left pad, and
         // everything right of the row up to the slot's end) is all ones,
         // written once
-        const int nslots = NST * 2 * RB * groups;
+        const int nslots = rect_xsets(a) * 2 * RB * groups;
         const int row_end = a.pad + tpr * NWT;
         for (int s = tid; s < nslots; s += blockDim.x) {
             uint32_t *p = sm + (size_t)s * a.slot_words;
@@ -431,6 +509,8 @@ __device__ __forceinline__ void rect_tile(const RectArgs &a, int bx, int by, uin
         }
         __syncthreads();
     }
+    RectTasks tasks;
+    tasks.init(tid, a.threads, RB, groups, a.tph);
 
     const int64_t sstride = a.sstride, dstride = a.dstride;
     // Row pointers advance by one stride per row; they are dereferenced only
@@ -538,29 +618,71 @@ __device__ __forceinline__ void rect_tile(const RectArgs &a, int bx, int by, uin
             }
         };
 
-        // Horizontal pass of the last stage on an exchanged chunk, and store.
-        auto hstore = [&](const uint32_t *xb, int u0, int L, int R) {
-            const bool all = Y0 + u0 + RB <= H;
-#pragma unroll 2
-            for (int i = 0; i < RB; ++i) {
-                uint32_t h[NWT];
-                rect_hpass<NWT, HM, HALO>(xb + i * row_words, L, R, a.m, h);
-                store(h, all || Y0 + u0 + i < H);
+        // Horizontal pass on an exchanged chunk as tasks of RECT_NWH words:
+        // the last stage stores rows u0 + i of its group's band, stage 1 of
+        // two writes its rows into `yb` for the stage-2 vertical pass.
+        constexpr int NWH = RECT_NWH;
+        auto htasks = [&](const uint32_t *xb, uint32_t *yb, int u0, int L, int R, auto last_flag) {
+            constexpr bool LAST = decltype(last_flag)::value;
+            int i = tasks.i0, gq = tasks.g0, sg = tasks.s0;
+#pragma unroll 1
+            for (int tk = tid; tk < tasks.total; tk += blockDim.x) {
+                const int off = i * row_words + gq * a.slot_words + a.pad + sg * NWH;
+                uint32_t h[NWH];
+                rect_hpass<NWH, HM, HALO>(xb + off, L, R, a.m, h);
+                if constexpr (LAST) {
+                    const int y = (bx * groups + gq) * band + u0 + i;
+                    if (y < H) {
+                        const int ws = strip0 - a.halo_words + sg * NWH;  // first word of the task
+                        uint32_t *p = a.dst + (int64_t)y * dstride + ws;
+                        uint32_t o[NWH];
+#pragma unroll
+                        for (int t = 0; t < NWH; ++t) o[t] = h[t] ^ inm_out;
+                        if (ws + NWH > a.nw_full) {
+                            // the row's last words: padding bits and words
+                            // past the pixels are written 0 (logic only, so
+                            // the warp stays on one path)
+#pragma unroll
+                            for (int t = 0; t < NWH; ++t) o[t] &= word_mask(ws + t, a.W);
+                        }
+                        if (a.vec16 && (ws & 3) == 0 && ws >= strip0 && ws + NWH <= strip_end) {
+                            RectVec<NWH>::st(p, o);
+                        } else {
+#pragma unroll
+                            for (int t = 0; t < NWH; ++t)
+                                if (ws + t >= strip0 && ws + t < strip_end) p[t] = o[t];
+                        }
+                    }
+                } else {
+                    RectVec<NWH>::st(yb + off, h);
+                }
+                sg += tasks.ds;
+                gq += tasks.dg;
+                i += tasks.di;
+                if (sg >= a.tph) {
+                    sg -= a.tph;
+                    ++gq;
+                }
+                if (gq >= groups) {
+                    gq -= groups;
+                    ++i;
+                }
             }
         };
 
-        // Two stages: stage-1 horizontal pass of an exchanged chunk, the stage-2
-        // vertical pass, and the rows into the stage-2 exchange buffer.
-        auto h1chunk = [&](int c1) {
-            const uint32_t *xb = X1 + (c1 & 1) * buf_words + own_off;
-            uint32_t *xo = X2 + (c1 & 1) * buf_words + own_off;
-            const int y10 = y1_first + c1 * RB - lagv;
+        // Two stages: the stage-2 vertical pass of a chunk of stage-1 rows
+        // handed back by the stage-1 horizontal tasks, into the stage-2
+        // exchange buffer.
+        auto v2chunk = [&](int c2) {
+            const uint32_t *yb = Y1 + (c2 & 1) * buf_words + own_off;
+            uint32_t *xo = X2 + (c2 & 1) * buf_words + own_off;
+            const int y10 = y1_first + c2 * RB - lagv;
             const bool f2free = y10 >= 0 && y10 + RB <= H;
-            const bool w2 = c1 * RB >= lag;
-#pragma unroll 2
+            const bool w2 = c2 * RB >= lag;
+#pragma unroll
             for (int i = 0; i < RB; ++i) {
                 uint32_t h[NWT], in2[NWT], o2[NWT];
-                rect_hpass<NWT, HM, HALO>(xb + i * row_words, a.L[0], a.R[0], a.m, h);
+                lds_own<NWT>(yb + i * row_words, h);
                 const int y1 = y10 + i;
                 const uint32_t fill2 = (f2free || (y1 >= 0 && y1 < H)) ? 0u : ONES;
 #pragma unroll
@@ -570,19 +692,23 @@ __device__ __forceinline__ void rect_tile(const RectArgs &a, int bx, int by, uin
             }
         };
 
-        const int last = XCH ? nch + NST - 1 : nch - 1;
+        const int last = XCH ? nch + (NST == 2 ? 2 : 0) : nch - 1;
         for (int c = 0; c <= last; ++c) {
             if constexpr (XCH) {
                 if constexpr (NST == 2) {
+                    const int c3 = c - 3;
+                    if (c3 >= 0 && c3 * RB >= lag)
+                        htasks(X2 + (c3 & 1) * buf_words, nullptr, c3 * RB - lag, a.L[1], a.R[1], std::true_type{});
                     const int c2 = c - 2;
-                    if (c2 >= 0 && c2 * RB >= lag)
-                        hstore(X2 + (c2 & 1) * buf_words + own_off, c2 * RB - lag, a.L[1], a.R[1]);
+                    if (c2 >= 0 && c2 < nch && c2 * RB >= lagv) v2chunk(c2);
                     const int c1 = c - 1;
-                    if (c1 >= 0 && c1 < nch && c1 * RB >= lagv) h1chunk(c1);
+                    if (c1 >= 0 && c1 < nch && c1 * RB >= lagv)
+                        htasks(X1 + (c1 & 1) * buf_words, Y1 + (c1 & 1) * buf_words, 0, a.L[0], a.R[0],
+                               std::false_type{});
                 } else {
                     const int c1 = c - 1;
                     if (c1 >= 0 && c1 * RB >= lag)
-                        hstore(X1 + (c1 & 1) * buf_words + own_off, c1 * RB - lag, a.L[0], a.R[0]);
+                        htasks(X1 + (c1 & 1) * buf_words, nullptr, c1 * RB - lag, a.L[0], a.R[0], std::true_type{});
                 }
             }
             if (c < nch) {

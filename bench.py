@@ -947,7 +947,7 @@ def run_ours(args):
                 "steps": e2e_steps, "pipelined": "copies of neighbouring steps overlap the launch",
                 "unpipelined_ms_per_step": round(e2e_serial_ms, 3),
                 "unpipelined_value": round(pix_step_rank * world / (e2e_serial_ms * 1e-3) / 1e9, 2)},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * batch.kernels,
         "clocks": clocks,
         "generation_s": round(t_gen, 2),
     }

@@ -412,6 +412,12 @@ MORPH_API morph_status morph_batch_plan_build(void *host_plan, size_t plan_bytes
 MORPH_API size_t morph_batch_workspace_size(const void *host_plan);
 /* Number of work items in a plan (-1 for an invalid plan). */
 MORPH_API int morph_batch_items(const void *host_plan);
+/* Kernel launches that one morph_batch_launch() of the plan makes (-1 for an
+ * invalid plan): jobs that neither depend on another job nor are depended
+ * on run as launches of the rectangle tiles, one per tile variant (packed
+ * jobs before the persistent kernel, RLE-path jobs after it, once it has
+ * encoded their source pages); the persistent kernel runs the rest. */
+MORPH_API int morph_batch_kernels(const void *host_plan);
 /* Test hook on a host plan (before it is copied to the device):
  * what = 0: set the wait limit to `value` ns (>= 1 ms; default 4 s);
  * what = 1: add `value` to the item count that the second phase of the first

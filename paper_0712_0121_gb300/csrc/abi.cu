@@ -11,6 +11,7 @@
 
 #include "morph_internal.cuh"
 #include "rect_tile.cuh"
+#include "rle_rect.cuh"
 
 namespace morph {
 
@@ -286,6 +287,30 @@ morph_status run_rle(int op, const morph_image *dst, const morph_image *src, Se 
     uint32_t *bmp = (uint32_t *)(base + L.bmp);
     int *st = device_status_ptr();
     cudaError_t e;
+    // windows taller than one row: the run-length-source tile (stage 1's
+    // within-line pass on the runs, every between-line pass and stage 2 on
+    // painted rows, both stages of an opening / closing in one pass) into
+    // the bitmap scratch, then one encode into dst
+    if (se.sh > 1) {
+        const int nw = (W + 31) / 32;
+        RectArgs a;
+        memset(&a, 0, sizeof(a));
+        a.dst = bmp;
+        a.dstride = nw;
+        a.W = W;
+        a.H = H;
+        a.nw_valid = nw;
+        a.nw_cover = nw;
+        if (rect_plan(a, op, se.sw, se.sh, se.ox, se.oy, 0, 0, 0, 0, true) == 0) {
+            const int dil1 = op == MORPH_DILATE || op == MORPH_CLOSE;
+            const RleSrc rs{src->row_ptr, reinterpret_cast<const uint32_t *>(src->runs), RowOp{dil1, se.sw, se.ox, W},
+                            src->capacity_runs};
+            e = launch_rle_rect_tile(a, rs, s);
+            if (e == cudaSuccess) e = launch_rle_from_bitmap(bmp, nw, W, H, rle_out(dst), counts, st, s);
+            if (e != cudaSuccess) return cuda_fail(e, "RLE morphology launch");
+            return MORPH_OK;
+        }
+    }
     if (op == MORPH_ERODE || op == MORPH_DILATE) {
         e = launch_rle_rect(rle_in(src), rle_out(dst), op == MORPH_DILATE, se.sw, se.sh, se.ox,
                             se.oy, counts, bmp, st, s);

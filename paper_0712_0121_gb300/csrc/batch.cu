@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "packed_tile.cuh"
+#include "rle_rect.cuh"
 #include "rle_tile.cuh"
 
 namespace morph {
@@ -115,6 +116,22 @@ struct BatchHeader {
     int64_t jobs_off, items_off, plan_bytes;
     int64_t ws_ctrl_bytes, ws_bytes;
     int64_t wait_limit_ns;
+    int32_t n_groups, pad0;
+    int64_t groups_off;
+};
+
+// Jobs that neither depend on another job nor are depended on run outside
+// the persistent kernel, as launches of the rectangle tiles over job tables:
+// packed jobs before it, RLE-path jobs (source runs -> both stages -> the
+// job's bitmap) after it, once it has encoded their sources.  One group per
+// tile variant and CTA size.
+struct TileGroup {
+    int32_t rle;         // 0: packed tile (before the persistent kernel); 1: RLE-source tile (after)
+    int32_t njobs, ctas, pad;
+    int64_t smem;        // dynamic shared memory of the launch
+    int64_t jobs_off;    // RectArgs[njobs] (packed) or RleJob[njobs] (RLE) in the plan
+    int64_t starts_off;  // int[njobs + 1]: first CTA of each job
+    RectArgs proto;      // variant and CTA size of the group
 };
 
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -429,11 +446,49 @@ morph_status berr(morph_status st, const char *msg, int job) {
 }
 
 // Build jobs and items; returns MORPH_OK and fills the vectors.
+struct GroupPlan {
+    TileGroup g;
+    std::vector<RectArgs> rect;
+    std::vector<RleJob> rle;
+    std::vector<int> starts;
+};
+
+bool same_variant(const RectArgs &x, const RectArgs &y) {
+    return x.nst == y.nst && x.nwt == y.nwt && x.vmode == y.vmode && x.hmode == y.hmode && x.halo == y.halo &&
+           x.threads == y.threads;
+}
+
+void add_to_group(std::vector<GroupPlan> &G, int rle, const RectArgs &ra, const RleJob *rj, size_t smem_bytes) {
+    GroupPlan *gp = nullptr;
+    for (auto &x : G)
+        if (x.g.rle == rle && same_variant(x.g.proto, ra)) gp = &x;
+    if (!gp) {
+        G.emplace_back();
+        gp = &G.back();
+        memset(&gp->g, 0, sizeof(gp->g));
+        gp->g.rle = rle;
+        gp->g.proto = ra;
+        gp->starts.push_back(0);
+    }
+    const int ctas = (int)(rect_grid(ra).x * rect_grid(ra).y);
+    if (rle) gp->rle.push_back(*rj);
+    else gp->rect.push_back(ra);
+    gp->starts.push_back(gp->starts.back() + ctas);
+    gp->g.njobs += 1;
+    gp->g.ctas += ctas;
+    if ((int64_t)smem_bytes > gp->g.smem) gp->g.smem = (int64_t)smem_bytes;
+}
+
 morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per_row,
                    std::vector<BatchJob> &J, std::vector<BatchItem> &I, int64_t &ws_ctrl,
-                   int64_t &ws_total, int &smem) {
+                   int64_t &ws_total, int &smem, std::vector<GroupPlan> &G) {
     J.assign(n, BatchJob{});
+    G.clear();
     smem = 0;
+    // jobs another job depends on stay inside the persistent kernel
+    std::vector<char> depended(n, 0);
+    for (int j = 0; j < n; ++j)
+        if (jobs[j].depends_on >= 0 && jobs[j].depends_on < j) depended[jobs[j].depends_on] = 1;
     // Default rows per row-range item: larger items amortise the per-item
     // cost (claim, dependency check, job fields) once the plan has enough
     // row-range work to keep every CTA busy with the larger items too.
@@ -510,6 +565,27 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
         const Clip c = clip_rect(W, H, q.se_w, q.se_h, q.origin_x, q.origin_y);
         const int nw_cover = d.fmt == MORPH_PACKED32 ? (W + 31) / 32 : 2 * ((W + 63) / 64);
         b.path = q.path;
+        const bool independent = q.depends_on < 0 && !depended[j];
+        const int band_hint = q.tile_rows ? q.tile_rows : tile_rows;
+        if (q.path == MORPH_PATH_PACKED && independent) {
+            RectArgs ra;
+            memset(&ra, 0, sizeof(ra));
+            ra.src = (const uint32_t *)s.words;
+            ra.sstride = s.stride_words * (Bs / 32);
+            ra.dst = (uint32_t *)d.words;
+            ra.dstride = d.stride_words * (Bd / 32);
+            ra.W = W;
+            ra.H = H;
+            ra.nw_valid = (W + 31) / 32;
+            ra.nw_cover = nw_cover;
+            if (rect_plan(ra, q.op, c.sw, c.sh, c.ox, c.oy, band_hint, 0, 0, 0) == 0) {
+                ra.band_auto = 0;
+                b.path = q.path;
+                b.nphase = 0;  // no work in the persistent kernel
+                add_to_group(G, 0, ra, nullptr, rect_smem_words(ra) * 4);
+                continue;
+            }
+        }
         if (q.path == MORPH_PATH_PACKED) {
             PackedArgs &a = b.pa;
             memset(&a, 0, sizeof(a));
@@ -561,6 +637,23 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
             // encode phases instead of encoding again.  Only jobs without a
             // user dependency share, and only encoders whose A stays intact
             // (a two-stage run pass writes its second stage into A).
+            // windows taller than a row, independent jobs: the run-length-
+            // source tile after the persistent kernel (which only encodes)
+            bool fused = false;
+            RectArgs fra;
+            if (c.sh > 1 && independent) {
+                memset(&fra, 0, sizeof(fra));
+                fra.dst = (uint32_t *)d.words;
+                fra.dstride = d.stride_words * (Bd / 32);
+                fra.W = W;
+                fra.H = H;
+                fra.nw_valid = (W + 31) / 32;
+                fra.nw_cover = nw_cover;
+                if (rect_plan(fra, q.op, c.sw, c.sh, c.ox, c.oy, band_hint, 0, 0, 0, true) == 0) {
+                    fra.band_auto = 0;
+                    fused = true;
+                }
+            }
             const bool a_rewritten = b.nst == 2 && c.sh == 1;
             int enc = -1;
             if (q.depends_on < 0) {
@@ -571,9 +664,11 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
             }
             b.off_counts = off; off += al((size_t)H * 4);
             b.off_nA = off; off += al(8);
-            b.off_nB = off; off += al(8);
-            b.off_rpB = off; off += al((size_t)(H + 1) * 4);
-            b.off_runsB = off; off += al((size_t)b.cap * 4);
+            if (!fused) {
+                b.off_nB = off; off += al(8);
+                b.off_rpB = off; off += al((size_t)(H + 1) * 4);
+                b.off_runsB = off; off += al((size_t)b.cap * 4);
+            }
             if (enc < 0 || a_rewritten) {
                 b.off_rpA = off; off += al((size_t)(H + 1) * 4);
                 b.off_runsA = off; off += al((size_t)b.cap * 4);
@@ -588,7 +683,7 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
                 b.off_srp = b.off_rpA;
                 b.off_sruns = b.off_runsA;
             }
-            if (b.nst == 2 && c.sh > 1) {
+            if (b.nst == 2 && c.sh > 1 && !fused) {
                 b.off_bmp = off;
                 off += al((size_t)H * ((W + 31) / 32) * 4);
             }
@@ -605,6 +700,17 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
                 add(IK_B2R_COUNT, rows_items, -1);
                 add(IK_SCAN, 1, -1);
                 add(IK_B2R_WRITE, rows_items, -1);
+            }
+            if (fused) {
+                RleJob rj;
+                rj.a = fra;
+                rj.off_row_ptr = b.off_srp;
+                rj.off_runs = b.off_sruns;
+                rj.op1 = RowOp{(q.op == MORPH_DILATE || q.op == MORPH_CLOSE) ? 1 : 0, c.sw, c.ox, W};
+                rj.cap = b.src_job == j ? b.cap : J[b.src_job].cap;
+                add_to_group(G, 1, fra, &rj, rle_rect_smem_words(fra) * 4);
+                b.nphase = p;  // the encode, if this job is its page's encoder
+                continue;
             }
             for (int st = 0; st < b.nst; ++st) {
                 // stage order: open = erode then dilate; close = dilate then erode
@@ -682,6 +788,18 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
     return MORPH_OK;
 }
 
+size_t group_tables_bytes(const GroupPlan &g) {
+    const size_t tab = g.g.rle ? g.rle.size() * sizeof(RleJob) : g.rect.size() * sizeof(RectArgs);
+    return al(tab) + al(g.starts.size() * sizeof(int));
+}
+
+size_t plan_size(const std::vector<BatchJob> &J, const std::vector<BatchItem> &I, const std::vector<GroupPlan> &G) {
+    size_t n = al(sizeof(BatchHeader)) + al(J.size() * sizeof(BatchJob)) + al(I.size() * sizeof(BatchItem)) +
+               al(G.size() * sizeof(TileGroup));
+    for (const auto &g : G) n += group_tables_bytes(g);
+    return n;
+}
+
 }  // namespace
 }  // namespace morph
 
@@ -694,10 +812,11 @@ size_t morph_batch_plan_bytes(const morph_job *jobs, int n_jobs, int tile_rows,
     if (!jobs || n_jobs < 1) return 0;
     std::vector<BatchJob> J;
     std::vector<BatchItem> I;
+    std::vector<GroupPlan> G;
     int64_t c, t;
     int smem;
-    if (build(jobs, n_jobs, tile_rows, rle_runs_per_row, J, I, c, t, smem) != MORPH_OK) return 0;
-    return al(sizeof(BatchHeader)) + al(J.size() * sizeof(BatchJob)) + al(I.size() * sizeof(BatchItem));
+    if (build(jobs, n_jobs, tile_rows, rle_runs_per_row, J, I, c, t, smem, G) != MORPH_OK) return 0;
+    return plan_size(J, I, G);
 }
 
 morph_status morph_batch_plan_build(void *host_plan, size_t plan_bytes, const morph_job *jobs,
@@ -708,9 +827,10 @@ morph_status morph_batch_plan_build(void *host_plan, size_t plan_bytes, const mo
     }
     std::vector<BatchJob> J;
     std::vector<BatchItem> I;
+    std::vector<GroupPlan> G;
     int64_t ctrl, total;
     int smem;
-    morph_status st = build(jobs, n_jobs, tile_rows, rle_runs_per_row, J, I, ctrl, total, smem);
+    morph_status st = build(jobs, n_jobs, tile_rows, rle_runs_per_row, J, I, ctrl, total, smem, G);
     if (st != MORPH_OK) return st;
     BatchHeader h;
     memset(&h, 0, sizeof(h));
@@ -720,7 +840,16 @@ morph_status morph_batch_plan_build(void *host_plan, size_t plan_bytes, const mo
     h.smem_bytes = smem;
     h.jobs_off = (int64_t)al(sizeof(BatchHeader));
     h.items_off = h.jobs_off + (int64_t)al(J.size() * sizeof(BatchJob));
-    h.plan_bytes = h.items_off + (int64_t)al(I.size() * sizeof(BatchItem));
+    h.groups_off = h.items_off + (int64_t)al(I.size() * sizeof(BatchItem));
+    h.n_groups = (int32_t)G.size();
+    int64_t toff = h.groups_off + (int64_t)al(G.size() * sizeof(TileGroup));
+    for (auto &g : G) {
+        g.g.jobs_off = toff;
+        toff += (int64_t)al(g.g.rle ? g.rle.size() * sizeof(RleJob) : g.rect.size() * sizeof(RectArgs));
+        g.g.starts_off = toff;
+        toff += (int64_t)al(g.starts.size() * sizeof(int));
+    }
+    h.plan_bytes = toff;
     h.ws_ctrl_bytes = ctrl;
     h.ws_bytes = total;
     h.wait_limit_ns = WAIT_LIMIT_NS;
@@ -733,7 +862,20 @@ morph_status morph_batch_plan_build(void *host_plan, size_t plan_bytes, const mo
     memcpy(p, &h, sizeof(h));
     memcpy(p + h.jobs_off, J.data(), J.size() * sizeof(BatchJob));
     memcpy(p + h.items_off, I.data(), I.size() * sizeof(BatchItem));
+    for (size_t k = 0; k < G.size(); ++k) {
+        const GroupPlan &g = G[k];
+        memcpy(p + h.groups_off + k * sizeof(TileGroup), &g.g, sizeof(TileGroup));
+        if (g.g.rle) memcpy(p + g.g.jobs_off, g.rle.data(), g.rle.size() * sizeof(RleJob));
+        else memcpy(p + g.g.jobs_off, g.rect.data(), g.rect.size() * sizeof(RectArgs));
+        memcpy(p + g.g.starts_off, g.starts.data(), g.starts.size() * sizeof(int));
+    }
     return MORPH_OK;
+}
+
+int morph_batch_kernels(const void *host_plan) {
+    const BatchHeader *h = (const BatchHeader *)host_plan;
+    if (!h || h->magic != PLAN_MAGIC) return -1;
+    return h->n_groups + (h->n_items > 0 ? 1 : 0);
 }
 
 size_t morph_batch_workspace_size(const void *host_plan) {
@@ -809,11 +951,43 @@ morph_status morph_batch_launch(const void *dev_plan, const void *host_plan, voi
             }
         }
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(workspace, 0, (size_t)h->ws_ctrl_bytes, s);
-    if (e == cudaSuccess) {
-        k_batch<<<n_ctas, BATCH_THREADS, smem, s>>>((const uint8_t *)dev_plan, (uint8_t *)workspace,
-                                                    device_status_ptr());
-        e = cudaGetLastError();
+    const uint8_t *dp = (const uint8_t *)dev_plan, *hp = (const uint8_t *)host_plan;
+    const TileGroup *groups = reinterpret_cast<const TileGroup *>(hp + h->groups_off);
+    // independent packed jobs: one launch of the rectangle tile per variant
+    for (int k = 0; e == cudaSuccess && k < h->n_groups; ++k) {
+        const TileGroup &g = groups[k];
+        if (g.rle || g.ctas < 1) continue;
+        const RectJobs mj{reinterpret_cast<const RectArgs *>(dp + g.jobs_off),
+                          reinterpret_cast<const int *>(dp + g.starts_off), g.njobs, g.ctas, (size_t)g.smem};
+        e = launch_rect(g.proto, s, &mj);
+        if (e != cudaSuccess) {
+            set_error("batch launch: packed group %d (stages %d, %d words, modes %d/%d/%d, %d threads, %d CTAs, "
+                      "%lld bytes shared): %s", k, g.proto.nst, g.proto.nwt, g.proto.vmode, g.proto.hmode,
+                      g.proto.halo, g.proto.threads, g.ctas, (long long)g.smem, cudaGetErrorString(e));
+            return MORPH_ECUDA;
+        }
+    }
+    if (h->n_items > 0) {
+        if (e == cudaSuccess) e = cudaMemsetAsync(workspace, 0, (size_t)h->ws_ctrl_bytes, s);
+        if (e == cudaSuccess) {
+            k_batch<<<n_ctas, BATCH_THREADS, smem, s>>>(dp, (uint8_t *)workspace, device_status_ptr());
+            e = cudaGetLastError();
+        }
+    }
+    // RLE-path jobs whose sources the persistent kernel has just encoded
+    for (int k = 0; e == cudaSuccess && k < h->n_groups; ++k) {
+        const TileGroup &g = groups[k];
+        if (!g.rle || g.ctas < 1) continue;
+        const RleJobs mj{reinterpret_cast<const RleJob *>(dp + g.jobs_off),
+                         reinterpret_cast<const int *>(dp + g.starts_off), (const uint8_t *)workspace, g.njobs,
+                         g.ctas, (size_t)g.smem};
+        e = launch_rle_rect_tile(g.proto, RleSrc{}, s, &mj);
+        if (e != cudaSuccess) {
+            set_error("batch launch: RLE group %d (stages %d, %d words, modes %d/%d/%d, %d threads, %d CTAs, "
+                      "%lld bytes shared): %s", k, g.proto.nst, g.proto.nwt, g.proto.vmode, g.proto.hmode,
+                      g.proto.halo, g.proto.threads, g.ctas, (long long)g.smem, cudaGetErrorString(e));
+            return MORPH_ECUDA;
+        }
     }
     if (e != cudaSuccess) {
         set_error("batch launch: %s", cudaGetErrorString(e));

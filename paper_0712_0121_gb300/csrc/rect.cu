@@ -4,6 +4,7 @@
 #include <cstdlib>
 #include <cstring>
 
+#include "rle_rect.cuh"
 #include "rect_tile.cuh"
 
 namespace morph {
@@ -86,7 +87,7 @@ void tile(RectArgs &a, int nwt, int threads) {
 }  // namespace
 
 int rect_plan(RectArgs &a, int op, int sw, int sh, int ox, int oy, int band_hint, int threads_hint,
-              int nwt_hint, size_t smem_budget) {
+              int nwt_hint, size_t smem_budget, bool rle_src) {
     const int rx = sw - 1 - ox, ry = sh - 1 - oy;
     a.sw = sw;
     a.sh = sh;
@@ -119,6 +120,13 @@ int rect_plan(RectArgs &a, int op, int sw, int sh, int ox, int oy, int band_hint
         a.halo = hw <= 1 ? 1 : (hw <= 2 ? 2 : 4);
     }
     a.vmode = sh == 1 ? RV_NONE : (sh <= 3 ? RV_W3 : RV_VHGW);
+    // a run-length source does stage 1's within-line pass on the runs: one
+    // stage has no within-line pass in the tile at all
+    if (rle_src && a.nst == 1) {
+        a.hmode = RH_NONE;
+        a.halo = 1;
+    }
+    auto smem_words = [&](const RectArgs &t) { return rle_src ? rle_rect_smem_words(t) : rect_smem_words(t); };
     const TilingOverride &ov = tiling_override();
     const bool force_v = ov.vmode >= 0 && sh >= 4 && (ov.vmode == RV_VHGW || (ov.vmode == RV_CNT && sh <= RECT_CNT_SH));
     if (force_v) a.vmode = ov.vmode;
@@ -139,9 +147,10 @@ int rect_plan(RectArgs &a, int op, int sw, int sh, int ox, int oy, int band_hint
         const int nwt = nwt_hint ? nwt_hint : cand[i][0];
         const int thr = threads_hint ? threads_hint : cand[i][1];
         tile(a, nwt, thr);
-        if (rect_smem_words(a) * 4 <= smem_budget || (nwt_hint && threads_hint)) done = true;
+        if (smem_words(a) * 4 <= smem_budget || (nwt_hint && threads_hint)) done = true;
     }
-    if (!done && ncand == 2) {
+    if (a.nst == 2 && a.vmode == RV_VHGW && !force_v && sh <= RECT_CNT_SH &&
+        (!done || smem_words(a) * 4 > smem_budget)) {
         a.vmode = RV_CNT;
         tile(a, nwt_hint ? nwt_hint : 2, threads_hint ? threads_hint : 256);
         done = true;
@@ -149,7 +158,8 @@ int rect_plan(RectArgs &a, int op, int sw, int sh, int ox, int oy, int band_hint
     if (!done) tile(a, 2, 128);
     // windows too tall for the rings of even the smallest tiling: the caller
     // falls back to the bit-sliced counter tile (O(log sh) state per word)
-    if (rect_smem_words(a) * 4 > RECT_SMEM_MAX) return -1;
+    if (smem_words(a) * 4 > RECT_SMEM_MAX) return -1;
+    if (rle_src && a.nstrips != 1) return -1;  // the run painter covers one strip
     // output rows per group: a few windows' worth, so that the rows read
     // twice (the window's extra rows) stay a small share; without a hint the
     // launch refines it from the resident CTAs (rect_fit_band)
@@ -210,13 +220,16 @@ int rect_sm_count(int dev) {
     return n[dev];
 }
 
-dim3 rect_grid(const RectArgs &a) {
-    return dim3((a.H + a.groups * a.band - 1) / (a.groups * a.band), a.nstrips);
+
+cudaError_t launch_rect(const RectArgs &a, cudaStream_t s, const RectJobs *mj) {
+    if (a.nst == 1) return a.nwt == 4 ? launch_rect_1_4(a, s, mj) : launch_rect_1_2(a, s, mj);
+    return a.nwt == 4 ? launch_rect_2_4(a, s, mj) : launch_rect_2_2(a, s, mj);
 }
 
-cudaError_t launch_rect(const RectArgs &a, cudaStream_t s) {
-    if (a.nst == 1) return a.nwt == 4 ? launch_rect_1_4(a, s) : launch_rect_1_2(a, s);
-    return a.nwt == 4 ? launch_rect_2_4(a, s) : launch_rect_2_2(a, s);
-}
+}  // namespace morph
 
+namespace morph {
+cudaError_t launch_rle_rect_tile(const RectArgs &a, const RleSrc &src, cudaStream_t s, const RleJobs *mj) {
+    return a.nwt == 4 ? launch_rle_rect_w4(a, src, s, mj) : launch_rle_rect_w2(a, src, s, mj);
+}
 }  // namespace morph

@@ -2,5 +2,7 @@
 #include "rect_kernels.cuh"
 
 namespace morph {
-cudaError_t launch_rect_1_4(const RectArgs &a, cudaStream_t s) { return rect_launch_nw<1, 4>(a, s); }
+cudaError_t launch_rect_1_4(const RectArgs &a, cudaStream_t s, const RectJobs *mj) {
+    return rect_launch_nw<1, 4>(a, s, mj);
+}
 }  // namespace morph

@@ -2,5 +2,7 @@
 #include "rect_kernels.cuh"
 
 namespace morph {
-cudaError_t launch_rect_2_2(const RectArgs &a, cudaStream_t s) { return rect_launch_nw<2, 2>(a, s); }
+cudaError_t launch_rect_2_2(const RectArgs &a, cudaStream_t s, const RectJobs *mj) {
+    return rect_launch_nw<2, 2>(a, s, mj);
+}
 }  // namespace morph

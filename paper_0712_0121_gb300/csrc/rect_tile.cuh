@@ -425,14 +425,71 @@ struct RectTasks {
     }
 };
 
+// Horizontal pass of one chunk of exchanged rows as tasks of RECT_NWH words
+// of one row.  LAST: the task's words of output row u0 + i of its group's
+// band go to the destination (complemented by inm_out, padding bits 0);
+// otherwise they go into `yb` at the same slot position.
+template <int HM, int HALO, bool LAST>
+__device__ __forceinline__ void rect_htasks(const RectArgs &a, const RectTasks &tasks, const uint32_t *xb,
+                                            uint32_t *yb, int u0, int L, int R, int bx, int strip0,
+                                            int strip_end, uint32_t inm_out, int row_words) {
+    constexpr int NWH = RECT_NWH;
+    const int groups = a.groups, band = a.band, H = a.H;
+    const int64_t dstride = a.dstride;
+    int i = tasks.i0, gq = tasks.g0, sg = tasks.s0;
+#pragma unroll 1
+    for (int tk = threadIdx.x; tk < tasks.total; tk += blockDim.x) {
+        const int off = i * row_words + gq * a.slot_words + a.pad + sg * NWH;
+        uint32_t h[NWH];
+        rect_hpass<NWH, HM, HALO>(xb + off, L, R, a.m, h);
+        if constexpr (LAST) {
+            const int y = (bx * groups + gq) * band + u0 + i;
+            if (y < H) {
+                const int ws = strip0 - a.halo_words + sg * NWH;  // first word of the task
+                uint32_t *p = a.dst + (int64_t)y * dstride + ws;
+                uint32_t o[NWH];
+#pragma unroll
+                for (int t = 0; t < NWH; ++t) o[t] = h[t] ^ inm_out;
+                if (ws + NWH > a.nw_full) {
+                    // the row's last words: padding bits and words past the
+                    // pixels are written 0 (logic only, so the warp stays on
+                    // one path)
+#pragma unroll
+                    for (int t = 0; t < NWH; ++t) o[t] &= word_mask(ws + t, a.W);
+                }
+                if (a.vec16 && (ws & 3) == 0 && ws >= strip0 && ws + NWH <= strip_end) {
+                    RectVec<NWH>::st(p, o);
+                } else {
+#pragma unroll
+                    for (int t = 0; t < NWH; ++t)
+                        if (ws + t >= strip0 && ws + t < strip_end) p[t] = o[t];
+                }
+            }
+        } else {
+            RectVec<NWH>::st(yb + off, h);
+        }
+        sg += tasks.ds;
+        gq += tasks.dg;
+        i += tasks.di;
+        if (sg >= a.tph) {
+            sg -= a.tph;
+            ++gq;
+        }
+        if (gq >= groups) {
+            gq -= groups;
+            ++i;
+        }
+    }
+}
+
 template <int NST, int NWT, int VM, int HM, int HALO>
 __device__ __forceinline__ void rect_tile(const RectArgs &a, int bx, int by, uint32_t *sm) {
     constexpr int RB = rect_rb(NST);
     constexpr bool XCH = HM != RH_NONE;  // rows exchanged between threads
     using RV = RectVec<NWT>;
     // a plan made for another variant or CTA size must not run this body
-    if (a.nwt != NWT || a.vmode != VM || a.hmode != HM || a.halo != HALO || a.nst != NST ||
-        (int)blockDim.x != a.threads)
+    if (a.nwt != NWT || a.vmode != VM || a.nst != NST || (int)blockDim.x != a.threads || a.hmode != HM ||
+        a.halo != HALO)
         return;
     const int tid = threadIdx.x;
     const int tpr = a.tpr, groups = a.groups, band = a.band, H = a.H, sh = a.sh;
@@ -618,56 +675,13 @@ __device__ __forceinline__ void rect_tile(const RectArgs &a, int bx, int by, uin
             }
         };
 
-        // Horizontal pass on an exchanged chunk as tasks of RECT_NWH words:
-        // the last stage stores rows u0 + i of its group's band, stage 1 of
-        // two writes its rows into `yb` for the stage-2 vertical pass.
-        constexpr int NWH = RECT_NWH;
+        // Horizontal pass on an exchanged chunk as tasks of RECT_NWH words
+        // (rect_htasks): the last stage stores rows u0 + i of its group's
+        // band, stage 1 of two writes its rows into `yb` for the stage-2
+        // vertical pass.
         auto htasks = [&](const uint32_t *xb, uint32_t *yb, int u0, int L, int R, auto last_flag) {
-            constexpr bool LAST = decltype(last_flag)::value;
-            int i = tasks.i0, gq = tasks.g0, sg = tasks.s0;
-#pragma unroll 1
-            for (int tk = tid; tk < tasks.total; tk += blockDim.x) {
-                const int off = i * row_words + gq * a.slot_words + a.pad + sg * NWH;
-                uint32_t h[NWH];
-                rect_hpass<NWH, HM, HALO>(xb + off, L, R, a.m, h);
-                if constexpr (LAST) {
-                    const int y = (bx * groups + gq) * band + u0 + i;
-                    if (y < H) {
-                        const int ws = strip0 - a.halo_words + sg * NWH;  // first word of the task
-                        uint32_t *p = a.dst + (int64_t)y * dstride + ws;
-                        uint32_t o[NWH];
-#pragma unroll
-                        for (int t = 0; t < NWH; ++t) o[t] = h[t] ^ inm_out;
-                        if (ws + NWH > a.nw_full) {
-                            // the row's last words: padding bits and words
-                            // past the pixels are written 0 (logic only, so
-                            // the warp stays on one path)
-#pragma unroll
-                            for (int t = 0; t < NWH; ++t) o[t] &= word_mask(ws + t, a.W);
-                        }
-                        if (a.vec16 && (ws & 3) == 0 && ws >= strip0 && ws + NWH <= strip_end) {
-                            RectVec<NWH>::st(p, o);
-                        } else {
-#pragma unroll
-                            for (int t = 0; t < NWH; ++t)
-                                if (ws + t >= strip0 && ws + t < strip_end) p[t] = o[t];
-                        }
-                    }
-                } else {
-                    RectVec<NWH>::st(yb + off, h);
-                }
-                sg += tasks.ds;
-                gq += tasks.dg;
-                i += tasks.di;
-                if (sg >= a.tph) {
-                    sg -= a.tph;
-                    ++gq;
-                }
-                if (gq >= groups) {
-                    gq -= groups;
-                    ++i;
-                }
-            }
+            rect_htasks<HM, HALO, decltype(last_flag)::value>(a, tasks, xb, yb, u0, L, R, bx, strip0, strip_end,
+                                                              inm_out, row_words);
         };
 
         // Two stages: the stage-2 vertical pass of a chunk of stage-1 rows
@@ -733,18 +747,39 @@ namespace morph {
 // (ox, oy) (already clipped to the image); hints of 0 take the defaults.
 // Returns 0, or -1 when the horizontal reach exceeds 128 pixels or the
 // window is too tall for the tile's shared memory (RECT_SMEM_MAX).
+// rle_src: plan for the run-length-source tile (rle_rect.cuh).
 int rect_plan(RectArgs &a, int op, int sw, int sh, int ox, int oy, int band_hint, int threads_hint,
-              int nwt_hint, size_t smem_budget);
-dim3 rect_grid(const RectArgs &a);
+              int nwt_hint, size_t smem_budget, bool rle_src = false);
+__host__ __device__ inline dim3 rect_grid(const RectArgs &a) {
+    return dim3((a.H + a.groups * a.band - 1) / (a.groups * a.band), a.nstrips);
+}
+// Several images of one variant in one launch (the batch's independent jobs).
+struct RectJobs {
+    const RectArgs *jobs;  // device: one plan per image (same variant and CTA size)
+    const int *starts;     // device: first CTA of each image, njobs + 1 entries
+    int njobs, ctas;
+    size_t smem;           // dynamic shared memory: the largest of the images' needs
+};
+// Image of CTA b: the j with starts[j] <= b < starts[j + 1].
+__device__ __forceinline__ int rect_job_of(const int *starts, int njobs, int b) {
+    int lo = 0, hi = njobs;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (starts[mid] <= b) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
 // Band height for `slots` resident CTAs: whole waves of CTAs over the image
 // when it is tall, else the smallest band that keeps the window's extra rows
 // a modest share.
 void rect_fit_band(RectArgs &a, int slots);
 int rect_sm_count(int dev);
-cudaError_t launch_rect(const RectArgs &a, cudaStream_t s);
-cudaError_t launch_rect_1_2(const RectArgs &a, cudaStream_t s);
-cudaError_t launch_rect_1_4(const RectArgs &a, cudaStream_t s);
-cudaError_t launch_rect_2_2(const RectArgs &a, cudaStream_t s);
-cudaError_t launch_rect_2_4(const RectArgs &a, cudaStream_t s);
+// mj: launch the images of a job table (plans of a's variant) instead of a.
+cudaError_t launch_rect(const RectArgs &a, cudaStream_t s, const RectJobs *mj = nullptr);
+cudaError_t launch_rect_1_2(const RectArgs &a, cudaStream_t s, const RectJobs *mj);
+cudaError_t launch_rect_1_4(const RectArgs &a, cudaStream_t s, const RectJobs *mj);
+cudaError_t launch_rect_2_2(const RectArgs &a, cudaStream_t s, const RectJobs *mj);
+cudaError_t launch_rect_2_4(const RectArgs &a, cudaStream_t s, const RectJobs *mj);
 
 }  // namespace morph

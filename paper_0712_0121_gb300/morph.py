@@ -131,6 +131,8 @@ def _load():
     lib.morph_batch_plan_build.restype = ci
     lib.morph_batch_workspace_size.argtypes = [vp]
     lib.morph_batch_workspace_size.restype = sz
+    lib.morph_batch_kernels.argtypes = [vp]
+    lib.morph_batch_kernels.restype = ci
     lib.morph_batch_items.argtypes = [vp]
     lib.morph_batch_items.restype = ci
     lib.morph_batch_plan_debug.argtypes = [vp, ci, ctypes.c_longlong]
@@ -584,6 +586,11 @@ class Batch:
         self.workspace = torch.empty(max(self.ws_bytes, 1), dtype=torch.uint8, device=device)
         self.n_items = int(_lib.morph_batch_items(hp))
         self.n_jobs = n
+
+    @property
+    def kernels(self) -> int:
+        """Kernel launches one :meth:`launch` makes."""
+        return int(_lib.morph_batch_kernels(self.host_plan.ctypes.data))
 
     def launch(self, stream=None, n_ctas: int = 0) -> None:
         _check(_lib.morph_batch_launch(self.dev_plan.data_ptr(), self.host_plan.ctypes.data,

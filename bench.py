@@ -243,6 +243,15 @@ def profile_traffic(name, pages):
         return None
 
 
+def measured_peak():
+    """(HBM GB/s, source) from MEASURED_PEAKS.json, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
 def time_launches(fn, steps, stream):
     import torch
     times = []
@@ -404,10 +413,12 @@ def run_uneven_batch(M, args, stream):
     t0 = time.perf_counter()
     specs = synth.config4_jobs(args.batch_pages)
     tuner = autotune.Tuner(cache_path=args.tune_cache, pages_per_class=4, reps=2)
-    ref = (2550, 3300)
-    if not tuner.table:
-        tuner.tune_grid(ref[0], ref[1], synth.CONFIG4_OPS, synth.CONFIG4_SES,
-                        densities=(0.01, 0.05, 0.15, 0.3), bands=(64, 128, 256, 512))
+    sizes = sorted({(j["W"], j["H"]) for j in specs})
+    if not all(tuner.tuned(W_, H_) for W_, H_ in sizes):
+        # every page size of the workload is its own class
+        for W_, H_ in sizes:
+            tuner.tune_grid(W_, H_, synth.CONFIG4_OPS, synth.CONFIG4_SES,
+                            densities=(0.01, 0.05, 0.15, 0.3), bands=(64, 128, 256, 512))
         tuner.save()
     t_tune = time.perf_counter() - t0
     imgs = pmap(lambda j: synth.config4_page(j)[0], specs)
@@ -415,7 +426,7 @@ def run_uneven_batch(M, args, stream):
     for j, img in zip(specs, imgs):
         src = M.pack(img, 64)
         dst = M.Packed.empty(j["W"], j["H"], 64)
-        path, band = tuner.choose(j["W"], j["H"], j["op"], j["se"], j["density"], ref_size=ref)
+        path, band = tuner.choose(j["W"], j["H"], j["op"], j["se"], j["density"])
         nrle += path == "rle"
         jobs.append(dict(op=j["op"], se=j["se"], path=path, tile_rows=band, src=src, dst=dst))
         npix += j["W"] * j["H"]
@@ -447,47 +458,81 @@ def run_uneven_batch(M, args, stream):
         loop()
     torch.cuda.synchronize()
     tl = statistics.mean(time_launches(loop, 3, stream))
+    # the fair baseline: the same per-page launches captured once in a CUDA
+    # graph (no host work per page left in the timed region)
+    pg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(pg):
+        loop()
+    for _ in range(2):
+        pg.replay()
+    torch.cuda.synchronize()
+    tg = statistics.mean(time_launches(pg.replay, 5, stream))
     st = M.sync_status()
+    peak = measured_peak()[0]
+    alg = sum(2 * j["src"].height * ((j["src"].width + 63) // 64) * 8 for j in jobs)
     return {"pages": len(jobs), "rle_path_pages": nrle, "megapixels": round(npix / 1e6, 1),
+            "size_classes_tuned": [list(sz) for sz in sizes],
             "batch_ms": round(tb, 3), "batch_pages_s": round(len(jobs) / tb * 1e3, 1),
             "batch_gpix_s": round(npix / tb / 1e6, 1),
+            "batch_roofline": {"alg_bytes": int(alg), "alg_gb_s": round(alg / tb / 1e6, 1),
+                               "frac": round(alg / tb / 1e6 / peak, 3),
+                               "note": "2 bits per pixel per page-operation (bitmap in and out)"},
+            "graph_per_page_ms": round(tg, 3), "graph_per_page_pages_s": round(len(jobs) / tg * 1e3, 1),
+            "speedup_vs_graph": round(tg / tb, 2),
             "per_page_loop_ms": round(tl, 3), "per_page_loop_pages_s": round(len(jobs) / tl * 1e3, 1),
-            "speedup": round(tl / tb, 2), "status": st, "tune_s": round(t_tune, 1)}
+            "speedup_vs_host_loop": round(tl / tb, 2), "status": st, "tune_s": round(t_tune, 1)}
+
+
+SERVE_RATES = (50, 200, 1000, 5000, 20000)
 
 
 def run_serving(M, args):
     """Poisson arrivals of 5100x6600 pages (near-blank, text, halftone,
     noise), pipeline close(31x1) -> open(3x3) -> dilate(1x15) -> RLE, 40 GB
-    budget: continuous batching vs an unbatched per-page server."""
+    budget: continuous batching vs an unbatched per-page server.  The pool
+    holds 256 device-resident pages (64 copies of each kind in distinct
+    memory, 1.08 GB: far more than L2), so requests read HBM.  Rates beyond
+    what one page at a time can sustain (5000 and 20000 pages/s) show the
+    batching at work; each run stops admitting after its arrival window plus
+    half of it again, and sustained pages/s counts completed requests."""
     import torch
     from paper_0712_0121_gb300 import synth
     from paper_0712_0121_gb300.serve import BatchExecutor, PerPageExecutor, Server, poisson_arrivals
     PW, PH = 5100, 6600
-    pool = [M.pack(synth.config3_page(kind, page=0)[0], 64) for kind in synth.CONFIG3_KINDS]
+    kinds = [M.pack(synth.config3_page(kind, page=0)[0], 64) for kind in synth.CONFIG3_KINDS]
+    pool = [M.Packed(kinds[k % len(kinds)].words.clone(), PW) for k in range(args.serve_pool)]
     bex = BatchExecutor(pool, PW, PH, n_slots=64, n_streams=4)
     pex = PerPageExecutor(pool, PW, PH)
     # warm-up both paths
-    Server(bex, 40e9).run(poisson_arrivals(2000.0, 16, 1), np.arange(16) % 4)
-    Server(pex, 40e9).run(poisson_arrivals(2000.0, 4, 1), np.arange(4) % 4)
+    Server(bex, 40e9).run(poisson_arrivals(2000.0, 64, 1), np.arange(64) % len(pool))
+    Server(pex, 40e9).run(poisson_arrivals(2000.0, 4, 1), np.arange(4) % len(pool))
     torch.cuda.synchronize()
-    out = {}
-    for rate in (50, 200, 1000):
+    out = {"pool_pages": len(pool), "pool_bytes": int(sum(p.words.numel() * 8 for p in pool)),
+           "slot_bytes": int(bex.slot_bytes), "slots": bex.n_slots, "budget_bytes": int(40e9)}
+    keep = ("p50_ms", "p99_ms", "queue_p99_ms", "sustained_pages_s", "mean_batch", "max_in_flight", "completed")
+    best = {"batched": 0.0, "per_page": 0.0}
+    for rate in SERVE_RATES:
         n = max(20, int(rate * args.serve_seconds))
         arr = poisson_arrivals(float(rate), n, seed=5000 + rate)
         pages = np.random.default_rng(rate).integers(0, len(pool), size=n)
+        limit = 1.5 * float(arr[-1])
         # the garbage collector stays off while requests are timed (both
         # modes alike): its pauses are host noise, not serving latency
         gc.collect()
         gc.disable()
         try:
-            sb = Server(bex, 40e9).run(arr, pages).summary()
-            sp = Server(pex, 40e9).run(arr, pages).summary()
+            sb = Server(bex, 40e9).run(arr, pages, time_limit=limit).summary()
+            sp = Server(pex, 40e9).run(arr, pages, time_limit=limit).summary()
         finally:
             gc.enable()
-        keep = ("p50_ms", "p99_ms", "sustained_pages_s", "mean_batch", "max_in_flight")
-        out[str(rate)] = {"requests": n,
-                          "batched": {k: (round(sb[k], 3) if isinstance(sb[k], float) else sb[k]) for k in keep},
-                          "per_page": {k: (round(sp[k], 3) if isinstance(sp[k], float) else sp[k]) for k in keep}}
+        rec = {"requests": n}
+        for name, sm in (("batched", sb), ("per_page", sp)):
+            rec[name] = {k: (round(sm[k], 3) if isinstance(sm[k], float) else sm[k]) for k in keep}
+            # highest offered rate served in full with p99 under 50 ms
+            if sm["completed"] == n and sm["p99_ms"] is not None and sm["p99_ms"] < 50.0:
+                best[name] = max(best[name], float(rate))
+        out[str(rate)] = rec
+    out["max_rate_p99_under_50ms"] = best
     st = M.sync_status()
     out["status"] = st
     return out
@@ -1018,7 +1063,8 @@ def main():
     ap.add_argument("--table-reps", type=int, default=5)
     ap.add_argument("--density-copies", type=int, default=48,
                     help="copies of each 5100x6600 page in the density-sweep stack (48: 203 MB)")
-    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-seconds", type=float, default=4.0, help="arrival window per rate")
+    ap.add_argument("--serve-pool", type=int, default=256, help="device-resident pages the requests draw from")
     ap.add_argument("--tune-cache", default=os.path.join("/tmp", "morph_tune_cache.json"))
     ap.add_argument("--probe", choices=["packed", "rle", "mask", "cc", "xpose", "line", "layout"], default=None,
                     help="run one standalone op on a tall page stack (ncu target) and exit")

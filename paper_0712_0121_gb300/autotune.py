@@ -123,6 +123,10 @@ class Tuner:
             os.replace(tmp, self.cache_path)
 
     # ------------------------------------------------------------ decision
+    def tuned(self, W, H) -> bool:
+        """Whether any class of this page size has been measured."""
+        return any(k.startswith("%dx%d:" % (W, H)) for k in self.table)
+
     def choose(self, W, H, op, se, density, ref_size=None):
         """(path, tile_rows) for one page; ``ref_size`` maps the page to the
         size its class was tuned at; untuned classes take the packed path with

@@ -120,14 +120,16 @@ struct BatchHeader {
     int64_t groups_off;
 };
 
-// Jobs that neither depend on another job nor are depended on run outside
-// the persistent kernel, as launches of the rectangle tiles over job tables:
-// packed jobs before it, RLE-path jobs (source runs -> both stages -> the
-// job's bitmap) after it, once it has encoded their sources.  One group per
-// tile variant and CTA size.
+// Jobs run outside the persistent kernel as launches of the rectangle tiles
+// over job tables, one group per tile variant and CTA size: packed jobs whose
+// dependency (if any) is itself such a packed job, level by level before the
+// persistent kernel; RLE-path jobs that neither depend on another job nor are
+// depended on (source runs -> both stages -> the job's bitmap) after it, once
+// it has encoded their sources.
 struct TileGroup {
     int32_t rle;         // 0: packed tile (before the persistent kernel); 1: RLE-source tile (after)
-    int32_t njobs, ctas, pad;
+    int32_t njobs, ctas;
+    int32_t level;       // packed: dependency level (a job's dependency runs at a lower level)
     int64_t smem;        // dynamic shared memory of the launch
     int64_t jobs_off;    // RectArgs[njobs] (packed) or RleJob[njobs] (RLE) in the plan
     int64_t starts_off;  // int[njobs + 1]: first CTA of each job
@@ -458,15 +460,17 @@ bool same_variant(const RectArgs &x, const RectArgs &y) {
            x.threads == y.threads;
 }
 
-void add_to_group(std::vector<GroupPlan> &G, int rle, const RectArgs &ra, const RleJob *rj, size_t smem_bytes) {
+void add_to_group(std::vector<GroupPlan> &G, int rle, int level, const RectArgs &ra, const RleJob *rj,
+                  size_t smem_bytes) {
     GroupPlan *gp = nullptr;
     for (auto &x : G)
-        if (x.g.rle == rle && same_variant(x.g.proto, ra)) gp = &x;
+        if (x.g.rle == rle && x.g.level == level && same_variant(x.g.proto, ra)) gp = &x;
     if (!gp) {
         G.emplace_back();
         gp = &G.back();
         memset(&gp->g, 0, sizeof(gp->g));
         gp->g.rle = rle;
+        gp->g.level = level;
         gp->g.proto = ra;
         gp->starts.push_back(0);
     }
@@ -489,6 +493,7 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
     std::vector<char> depended(n, 0);
     for (int j = 0; j < n; ++j)
         if (jobs[j].depends_on >= 0 && jobs[j].depends_on < j) depended[jobs[j].depends_on] = 1;
+    std::vector<int> glevel(n, -1);  // level of a packed job run as a grouped launch
     // Default rows per row-range item: larger items amortise the per-item
     // cost (claim, dependency check, job fields) once the plan has enough
     // row-range work to keep every CTA busy with the larger items too.
@@ -516,6 +521,12 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
             return berr(MORPH_EINVAL, "depends_on must be -1 or an earlier job", j);
         b.dep = q.depends_on;
         b.dep_phase = b.dep >= 0 ? J[b.dep].nphase - 1 : 0;
+        // a job that waits for a grouped packed job runs after every group
+        // level in stream order: no wait inside the persistent kernel
+        if (b.dep >= 0 && glevel[b.dep] >= 0) {
+            b.dep = -1;
+            b.dep_phase = 0;
+        }
         b.src_job = j;
         if (q.op == MORPH_TO_RLE) {
             if (!packed(s) || d.fmt != MORPH_RLE) return berr(MORPH_EINVAL, "MORPH_TO_RLE needs a packed src and an RLE dst", j);
@@ -567,7 +578,8 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
         b.path = q.path;
         const bool independent = q.depends_on < 0 && !depended[j];
         const int band_hint = q.tile_rows ? q.tile_rows : tile_rows;
-        if (q.path == MORPH_PATH_PACKED && independent) {
+        const bool chainable = q.depends_on < 0 || glevel[q.depends_on] >= 0;
+        if (q.path == MORPH_PATH_PACKED && chainable) {
             RectArgs ra;
             memset(&ra, 0, sizeof(ra));
             ra.src = (const uint32_t *)s.words;
@@ -582,7 +594,8 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
                 ra.band_auto = 0;
                 b.path = q.path;
                 b.nphase = 0;  // no work in the persistent kernel
-                add_to_group(G, 0, ra, nullptr, rect_smem_words(ra) * 4);
+                glevel[j] = q.depends_on < 0 ? 0 : glevel[q.depends_on] + 1;
+                add_to_group(G, 0, glevel[j], ra, nullptr, rect_smem_words(ra) * 4);
                 continue;
             }
         }
@@ -708,7 +721,7 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
                 rj.off_runs = b.off_sruns;
                 rj.op1 = RowOp{(q.op == MORPH_DILATE || q.op == MORPH_CLOSE) ? 1 : 0, c.sw, c.ox, W};
                 rj.cap = b.src_job == j ? b.cap : J[b.src_job].cap;
-                add_to_group(G, 1, fra, &rj, rle_rect_smem_words(fra) * 4);
+                add_to_group(G, 1, 0, fra, &rj, rle_rect_smem_words(fra) * 4);
                 b.nphase = p;  // the encode, if this job is its page's encoder
                 continue;
             }
@@ -786,6 +799,36 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
                     I.push_back(BatchItem{j, (int16_t)p, (int16_t)J[j].phase_kind[p], k});
         }
     return MORPH_OK;
+}
+
+// Streams the batch launch forks its tile groups onto (per device, created
+// once, never destroyed), with the events of the fork and of the join.  The
+// launch sequence holds the device's mutex, so one set serves every caller.
+constexpr int AUX_STREAMS = 4;
+struct AuxStreams {
+    std::mutex mu;
+    bool made = false;
+    cudaStream_t st[AUX_STREAMS];
+    cudaEvent_t fork, kb_done, join[AUX_STREAMS];
+};
+AuxStreams *aux_streams(int dev, cudaError_t &e) {
+    static AuxStreams a[64];
+    e = cudaSuccess;
+    if (dev < 0 || dev >= 64) {
+        e = cudaErrorInvalidDevice;
+        return nullptr;
+    }
+    return &a[dev];
+}
+cudaError_t make_aux(AuxStreams &a) {
+    if (a.made) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < AUX_STREAMS && e == cudaSuccess; ++k) e = cudaStreamCreateWithFlags(&a.st[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.kb_done, cudaEventDisableTiming);
+    for (int k = 0; k < AUX_STREAMS && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&a.join[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) a.made = true;
+    return e;
 }
 
 size_t group_tables_bytes(const GroupPlan &g) {
@@ -953,19 +996,69 @@ morph_status morph_batch_launch(const void *dev_plan, const void *host_plan, voi
     }
     const uint8_t *dp = (const uint8_t *)dev_plan, *hp = (const uint8_t *)host_plan;
     const TileGroup *groups = reinterpret_cast<const TileGroup *>(hp + h->groups_off);
-    // independent packed jobs: one launch of the rectangle tile per variant
-    for (int k = 0; e == cudaSuccess && k < h->n_groups; ++k) {
-        const TileGroup &g = groups[k];
-        if (g.rle || g.ctas < 1) continue;
-        const RectJobs mj{reinterpret_cast<const RectArgs *>(dp + g.jobs_off),
-                          reinterpret_cast<const int *>(dp + g.starts_off), g.njobs, g.ctas, (size_t)g.smem};
-        e = launch_rect(g.proto, s, &mj);
-        if (e != cudaSuccess) {
-            set_error("batch launch: packed group %d (stages %d, %d words, modes %d/%d/%d, %d threads, %d CTAs, "
-                      "%lld bytes shared): %s", k, g.proto.nst, g.proto.nwt, g.proto.vmode, g.proto.hmode,
-                      g.proto.halo, g.proto.threads, g.ctas, (long long)g.smem, cudaGetErrorString(e));
-            return MORPH_ECUDA;
+    int npk = 0, nrl = 0;
+    for (int k = 0; k < h->n_groups; ++k) {
+        if (groups[k].ctas < 1) continue;
+        if (groups[k].rle) ++nrl;
+        else ++npk;
+    }
+    // Tile groups run on the device's auxiliary streams, forked from and
+    // joined back into the caller's stream: the packed groups of each level
+    // together, then the persistent kernel, then the RLE groups (they read
+    // its encodes).
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    AuxStreams *ax = nullptr;
+    if (e == cudaSuccess) ax = aux_streams(dev, e);
+    if (e == cudaSuccess && npk + nrl == 0) ax = nullptr;
+    std::unique_lock<std::mutex> lk;
+    if (ax) {
+        lk = std::unique_lock<std::mutex>(ax->mu);
+        e = make_aux(*ax);
+    }
+    int used = 0;
+    auto aux_for = [&](int i) {
+        const int k = i % AUX_STREAMS;
+        if (k + 1 > used) used = k + 1;
+        return ax->st[k];
+    };
+    // fork the auxiliary streams from the caller's stream, and join them back
+    auto fork = [&](cudaEvent_t ev) {
+        cudaError_t r = cudaEventRecord(ev, s);
+        for (int k = 0; r == cudaSuccess && k < AUX_STREAMS; ++k) r = cudaStreamWaitEvent(ax->st[k], ev, 0);
+        return r;
+    };
+    auto join = [&]() {
+        cudaError_t r = cudaSuccess;
+        for (int k = 0; r == cudaSuccess && k < AUX_STREAMS; ++k) {
+            r = cudaEventRecord(ax->join[k], ax->st[k]);
+            if (r == cudaSuccess) r = cudaStreamWaitEvent(s, ax->join[k], 0);
         }
+        return r;
+    };
+    // packed groups level by level (a level's jobs read the level below);
+    // the persistent kernel follows the last level
+    int maxlevel = -1;
+    for (int k = 0; k < h->n_groups; ++k)
+        if (!groups[k].rle && groups[k].ctas > 0 && groups[k].level > maxlevel) maxlevel = groups[k].level;
+    int gi = 0;
+    for (int lv = 0; e == cudaSuccess && lv <= maxlevel; ++lv) {
+        e = fork(ax->fork);
+        for (int k = 0; e == cudaSuccess && k < h->n_groups; ++k) {
+            const TileGroup &g = groups[k];
+            if (g.rle || g.ctas < 1 || g.level != lv) continue;
+            const RectJobs mj{reinterpret_cast<const RectArgs *>(dp + g.jobs_off),
+                              reinterpret_cast<const int *>(dp + g.starts_off), g.njobs, g.ctas, (size_t)g.smem};
+            e = launch_rect(g.proto, aux_for(gi++), &mj);
+            if (e != cudaSuccess) {
+                set_error("batch launch: packed group %d (stages %d, %d words, modes %d/%d/%d, %d threads, %d "
+                          "CTAs, %lld bytes shared): %s", k, g.proto.nst, g.proto.nwt, g.proto.vmode,
+                          g.proto.hmode, g.proto.halo, g.proto.threads, g.ctas, (long long)g.smem,
+                          cudaGetErrorString(e));
+                return MORPH_ECUDA;
+            }
+        }
+        if (e == cudaSuccess) e = join();
     }
     if (h->n_items > 0) {
         if (e == cudaSuccess) e = cudaMemsetAsync(workspace, 0, (size_t)h->ws_ctrl_bytes, s);
@@ -974,14 +1067,15 @@ morph_status morph_batch_launch(const void *dev_plan, const void *host_plan, voi
             e = cudaGetLastError();
         }
     }
-    // RLE-path jobs whose sources the persistent kernel has just encoded
+    // RLE groups read the encodes of the persistent kernel: fork after it
+    if (nrl > 0 && e == cudaSuccess) e = fork(ax->kb_done);
     for (int k = 0; e == cudaSuccess && k < h->n_groups; ++k) {
         const TileGroup &g = groups[k];
         if (!g.rle || g.ctas < 1) continue;
         const RleJobs mj{reinterpret_cast<const RleJob *>(dp + g.jobs_off),
                          reinterpret_cast<const int *>(dp + g.starts_off), (const uint8_t *)workspace, g.njobs,
                          g.ctas, (size_t)g.smem};
-        e = launch_rle_rect_tile(g.proto, RleSrc{}, s, &mj);
+        e = launch_rle_rect_tile(g.proto, RleSrc{}, aux_for(gi++), &mj);
         if (e != cudaSuccess) {
             set_error("batch launch: RLE group %d (stages %d, %d words, modes %d/%d/%d, %d threads, %d CTAs, "
                       "%lld bytes shared): %s", k, g.proto.nst, g.proto.nwt, g.proto.vmode, g.proto.hmode,
@@ -989,6 +1083,8 @@ morph_status morph_batch_launch(const void *dev_plan, const void *host_plan, voi
             return MORPH_ECUDA;
         }
     }
+    if (nrl > 0 && e == cudaSuccess) e = join();
+    (void)used;
     if (e != cudaSuccess) {
         set_error("batch launch: %s", cudaGetErrorString(e));
         return MORPH_ECUDA;

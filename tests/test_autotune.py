@@ -17,6 +17,7 @@ def test_choose_by_density(tmp_path):
     assert t.choose(100, 200, "open", (31, 31), 0.25) == ("packed", 128)
     assert t.choose(5, 5, "open", (31, 31), 0.004, ref_size=(100, 200)) == ("rle", 128)
     assert t.choose(100, 200, "close", (3, 3), 0.01) == ("packed", 0)
+    assert t.tuned(100, 200) and not t.tuned(5, 5)
     assert t.crossover(100, 200, "open", (31, 31)) == [0.005, 0.05]
 
 

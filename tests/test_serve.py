@@ -78,3 +78,18 @@ def test_percentiles_and_poisson_rate():
     a = poisson_arrivals(1000.0, 20000, seed=3)
     assert np.all(np.diff(a) > 0)
     assert 20000 / a[-1] == pytest.approx(1000.0, rel=0.03)
+
+
+def test_budget_binds_with_letter_and_600dpi_slot_sizes():
+    """Slots of the bench's 5100 x 6600 pipeline (three intermediate pages of
+    4.2 MB and an RLE output with room for W/8 + 4 runs per row: about 30 MB)
+    never bind a 40 GB budget with 64 slots (1.9 GB), which is why the bench
+    reports the slot bytes beside the budget; a budget of 3.5 slots does bind
+    and caps the requests in flight at 3."""
+    page = 6600 * ((5100 + 63) // 64) * 8
+    slot = 3 * page + 6600 * (5100 // 8 + 4) * 4 + 4 * 6601
+    assert 64 * slot < 40e9
+    srv, ex, st = run(rate=20000.0, n=300, budget=3.5 * slot, slot_bytes=slot, n_slots=64, service=5e-3)
+    assert st.completed == 300
+    assert st.max_in_flight == 3
+    assert st.max_in_flight_bytes <= 3.5 * slot

@@ -44,12 +44,16 @@ def test_served_results_equal_alone(pool, path):
     ex = BatchExecutor([p for _, p in pool], W, H, n_slots=48, n_streams=3, runs_per_row=rpr, path=path)
     srv = Server(ex, budget_bytes=40e9)
     n = 40
-    arr = poisson_arrivals(3000.0, n, seed=11)
+    # 16 requests arrive together, the rest as a fast Poisson stream: they
+    # are admitted in shared rounds and are on the GPU at the same time
+    arr = np.concatenate([np.zeros(16), 1e-3 + poisson_arrivals(3000.0, n - 16, seed=11)])
     pages = np.arange(n) % len(pool)
     st = srv.run(arr, pages)
     torch.cuda.synchronize()
     assert M.sync_status() == M.MORPH_OK
     assert st.completed == n
+    assert max(st.batch_sizes) > 1, "no admission round held more than one request"
+    assert st.max_in_flight > 1, "no two requests were in flight together"
     # results live in the slots until reused: check the last occupant of each slot
     last = {}
     for r in srv.requests:

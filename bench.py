@@ -3,20 +3,25 @@
 
 Workload (letter pages at 300 dpi): B distinct seeded 2550 x 3300 document
 pages (8 % ink, 2-3 columns, ruled lines, boxes) resident in HBM.  One step =
-ONE persistent batch launch that opens and closes every page with each of the
-rectangles 3x3, 7x7, 15x15, 31x31, 51x51, 1x51 and 51x1, once on the packed
-path (fused tile kernel) and once on the RLE path (bitmap -> runs, run and
-between-line passes, runs -> bitmap), i.e. 28 page-operations per page.  The
-batch planner encodes each page to runs once per step and its 14 RLE jobs
-read those runs (the algorithmic bytes count that encode once per page).
+one batch launch (captured as a CUDA graph) that opens and closes every page
+with each of the rectangles 3x3, 7x7, 15x15, 31x31, 51x51, 1x51 and 51x1,
+once on the packed path and once on the RLE path, i.e. 28 page-operations per
+page.  The batch planner groups the packed jobs by tile variant (one launch of
+the rectangle tile per group), encodes each page to runs once in the
+persistent batch kernel, and runs the RLE jobs as groups of the run-length
+source tile that read those runs (the algorithmic bytes count the encode once
+per page): ten kernel launches per step on the letter workload.
 
 Metric: page-operation pixels per second (Gpix/s) over the whole step.  The
 JSON line also carries pages/s, the packed-only and RLE-only rates (timed as
-separate batches), the roofline of the batch kernel (algorithmic bytes /
-launch time vs the measured HBM copy bandwidth), an end-to-end figure through
-the same API with host buffers (H2D of the pages and D2H of every result
-inside the timed region), sampled SM clocks, and the CPU oracle timed on a
-bounded sample of the same workload on this host's cores.
+separate batches), the roofline of the dominant kernel (the grouped launch of
+the two-stage tile with counter vertical passes: open / close by 15x15, 31x31
+and 51x51 on the packed path, timed alone with CUDA events, algorithmic
+bytes against the measured HBM copy bandwidth), the same ratio for the whole
+step, an end-to-end figure through the same API with host buffers (H2D of the
+pages and D2H of every result inside the timed region), sampled SM clocks,
+and the CPU oracle timed on a bounded sample of the same workload on this
+host's cores.
 
 --impl reference times the CPU oracle (plain C on unpacked bytes) on the same
 workload, a bounded sample per step.
@@ -43,7 +48,8 @@ METRIC = "Gpix/s rect erode/dilate (packed, RLE) vs HBM peak; batched pages/s; p
 UNIT = "Gpix/s"
 WORKLOAD = ("letter-300dpi: 2550x3300 text pages, open+close x {3,7,15,31,51 squares, "
             "1x51, 51x1}, packed and RLE paths (a page's RLE jobs share one bitmap->RLE "
-            "encode per step), one persistent batch launch per step")
+            "encode per step), one batch launch per step (grouped tile kernels and the "
+            "persistent encode kernel, one CUDA graph)")
 
 
 def env_rank():
@@ -205,19 +211,25 @@ def whole_job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
     return units_per_rank * world / (ms_max * 1e-3)
 
 
-# Sources the batch kernel and its planner are built from (the entry points
-# of the single-image operations, masks and the no-alloc path are not).
-BATCH_SOURCES = ("batch.cu", "packed.cu", "rle.cu", "morph_internal.cuh", "packed_tile.cuh",
-                 "rle_tile.cuh", "counters.cuh", "cp_async.cuh")
+# The dominant kernel of a step (the largest share of the step's launch
+# list): the grouped launch of the two-stage rectangle tile whose vertical
+# passes use bit-sliced run counters, which runs the packed open / close jobs
+# of these rectangles (their van Herk / Gil-Werman rings for two stages do
+# not fit two CTAs per SM).
+DOMINANT_SES = ((15, 15), (31, 31), (51, 51))
+DOMINANT_KERNEL = ("k_rect<2 stages, 2 words/thread, counter vertical, log horizontal>: one grouped "
+                   "launch of the packed open/close jobs by 15x15, 31x31, 51x51")
+# Sources that kernel and its planner are built from.
+DOMINANT_SOURCES = ("rect_tile.cuh", "rect_kernels.cuh", "rect.cu", "rect_k2w2.cu", "counters.cuh",
+                    "morph_internal.cuh", "batch.cu")
 
 
 def csrc_digest():
-    """SHA-256 over the sources of the batch kernel and the ABI header (ties
-    a profile record of that kernel to the code it was taken from)."""
+    """SHA-256 over the sources of the dominant kernel (ties a profile record
+    of that kernel to the code it was taken from)."""
     import hashlib
     h = hashlib.sha256()
-    files = [os.path.join(ROOT, "paper_0712_0121_gb300", "csrc", f) for f in BATCH_SOURCES]
-    files.append(os.path.join(ROOT, "include", "morph.h"))
+    files = [os.path.join(ROOT, "paper_0712_0121_gb300", "csrc", f) for f in DOMINANT_SOURCES]
     for f in files:
         with open(f, "rb") as fh:
             h.update(os.path.basename(f).encode() + b"\0" + fh.read())
@@ -860,7 +872,25 @@ def run_ours(args):
     # and row offsets once per page, not once per job
     rle_per_page = sum(1 for j in jobs if j["path"] == "rle") // B
     bytes_launch -= B * max(0, rle_per_page - 1) * encode_bytes(mean_runs_in)
-    achieved = bytes_launch / (ms * 1e-3) / 1e9
+    step_achieved = bytes_launch / (ms * 1e-3) / 1e9
+
+    # the dominant kernel alone: a batch of just its jobs is one grouped
+    # launch of that tile (forked onto an auxiliary stream and joined back,
+    # so events on this stream bracket it), timed like the steps
+    dom = [j for j in jobs if j["path"] == "packed" and tuple(j["se"]) in DOMINANT_SES]
+    bdom = M.Batch(dom, rle_runs_per_row=args.rle_runs_per_row)
+    gdom = bdom.capture()
+    for _ in range(3):
+        gdom.replay()
+    torch.cuda.synchronize()
+    dom_ms = statistics.mean(time_launches(gdom.replay, max(5, args.steps // 2), stream))
+    st = M.sync_status()
+    if st != M.MORPH_OK:
+        raise RuntimeError("device status %d after the dominant-kernel launches" % st)
+    dom_bytes = sum(alg_bytes("packed", 0, 0) for _ in dom)
+    dom_kernels = bdom.kernels
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    del bdom, gdom
 
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peak, peak_src = 6782.1, "fallback"
@@ -984,9 +1014,14 @@ def run_ours(args):
         "packed_gpix_s": round(sub["packed"], 1), "rle_gpix_s": round(sub["rle"], 1),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": profile_traffic("k_batch_letter300_dram.md", B),
-                     "kernel": "k_batch (persistent batch launch)", "peak_source": peak_src,
-                     "alg_bytes_per_launch": int(bytes_launch)},
+                     "traffic": profile_traffic("k_rect_open_close_cnt_letter_dram.md", B),
+                     "kernel": DOMINANT_KERNEL, "peak_source": peak_src,
+                     "page_ops_per_launch": len(dom), "launches": dom_kernels,
+                     "alg_bytes_per_launch": int(dom_bytes), "ms_per_launch": round(dom_ms, 4),
+                     "alg_bytes_per_page_op": 2 * H * NW * 8},
+        "step_roofline": {"alg_bytes_per_step": int(bytes_launch), "achieved": round(step_achieved, 1),
+                          "unit": "GB/s", "frac": round(step_achieved / peak, 4),
+                          "kernels_per_step": batch.kernels},
         "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 3),
                 "steps": e2e_steps, "pipelined": "copies of neighbouring steps overlap the launch",

@@ -353,31 +353,53 @@ MORPH_API morph_status morph_run_length_hist(int64_t *black_hist, int64_t *white
 
 /* ----------------------------------------------------------------- batch --
  * Many uneven pages, each with its own op, rectangle and path, in ONE
- * persistent kernel launch.  A job reads a packed src page and writes a
+ * morph_batch_launch() call.  A job reads a packed src page and writes a
  * packed dst page (same size, no overlap), or with MORPH_TO_RLE converts it
  * into an RLE dst.  A job may depend on one earlier job (depends_on), which
  * chains per-page pipelines (e.g. close -> open -> dilate -> to RLE) inside
- * one launch; items are ordered so that every wait points backwards.  path MORPH_PATH_PACKED runs the
- * fused tile kernel on the page; MORPH_PATH_RLE converts the page to runs,
- * runs the RLE operation and converts back, all inside the same launch.  The
- * choice per page is the caller's (the Python autotuner picks it by ink
- * density and rectangle).
+ * one call.  path MORPH_PATH_PACKED runs the fused rectangle tile on the
+ * page; MORPH_PATH_RLE converts the page to runs, runs the RLE operation on
+ * them and writes the result back as a bitmap.  The choice per page is the
+ * caller's (the Python autotuner picks it by ink density and rectangle).
+ *
+ * How a call runs (the operations are those of sections "2D Morphological
+ * Operators for Rectangular Masks" and "Conversion Between Image Formats"; the
+ * grouping is this library's):
+ *  - packed-path jobs with no dependency, or whose dependency is itself such
+ *    a job, run as grouped launches of the rectangle tile: one launch per
+ *    tile variant and dependency level, over a device table of the level's
+ *    jobs of that variant; the levels run in order, the launches of a level
+ *    concurrently on the library's four auxiliary streams of the device,
+ *    forked from and joined back into the caller's stream;
+ *  - then one persistent kernel runs every other job (RLE-path jobs with a
+ *    dependency or without a between-line pass, MORPH_TO_RLE jobs, packed
+ *    jobs the tile cannot plan) and the bitmap -> RLE encodes of the
+ *    source pages of RLE-path jobs;
+ *  - then RLE-path jobs that neither depend on a job nor are depended on and
+ *    have a between-line pass run as grouped launches of the run-length
+ *    source tile, which read the persistent kernel's encodes (both stages of
+ *    an opening or closing in one pass).
+ * morph_batch_kernels() returns the number of kernel launches of one call.
  *
  * Use: morph_batch_plan_bytes() -> a host buffer; morph_batch_plan_build()
  * fills it (all checks happen here); the caller copies the plan to device
  * memory and calls morph_batch_launch() with that copy, the host plan and a
- * workspace of morph_batch_workspace_size() bytes (counters and the RLE
- * buffers of RLE-path jobs).  The launch does no host work beyond one memset
- * of the counters and the kernel launch, so it can be captured in a CUDA
- * graph and replayed while the plan, workspace and pages stay valid.
- * Work items are claimed from a device queue in plan order; an item waits
- * (bounded spin, acquire loads) only for items of smaller index, which are
- * already held by running CTAs, so the launch cannot deadlock.  A wait longer
- * than the plan's limit (4 s) latches MORPH_ETIMEOUT and stops every CTA; an RLE buffer that is
- * too small latches MORPH_ECAPACITY and leaves that job's dst unwritten (and, when it is the
- * buffer of a shared source encode, the dst of every job sharing it).  RLE-path jobs without
- * depends_on that read the same source page (same words, stride, format and size) share one
- * bitmap -> RLE encode of it: the first such job encodes, the others read its runs.
+ * workspace of morph_batch_workspace_size() bytes (counters, encodes and the
+ * RLE buffers of RLE-path jobs).  The launch does no host work beyond
+ * kernel launches, one memset of the counters and the event records and
+ * waits of the fork and join, so it can be captured in a CUDA graph and
+ * replayed while the plan, workspace and pages stay valid.  Launches of one
+ * device from several host threads share its auxiliary streams (a mutex
+ * orders their use).
+ * In the persistent kernel, work items are claimed from a device queue in
+ * plan order; an item waits (bounded spin, acquire loads) only for items of
+ * smaller index, which are already held by running CTAs, so the launch
+ * cannot deadlock.  A wait longer than the plan's limit (4 s) latches
+ * MORPH_ETIMEOUT and stops every CTA; an RLE buffer that is too small latches
+ * MORPH_ECAPACITY and leaves that job's dst unwritten (and, when it is the
+ * buffer of a shared source encode, the dst of every job sharing it).
+ * RLE-path jobs without depends_on that read the same source page (same
+ * words, stride, format and size) share one bitmap -> RLE encode of it.
  *
  * tile_rows: for jobs whose own tile_rows is 0, the row-band height of
  * packed tiles and the rows per work item of RLE-path and MORPH_TO_RLE jobs
@@ -413,10 +435,8 @@ MORPH_API size_t morph_batch_workspace_size(const void *host_plan);
 /* Number of work items in a plan (-1 for an invalid plan). */
 MORPH_API int morph_batch_items(const void *host_plan);
 /* Kernel launches that one morph_batch_launch() of the plan makes (-1 for an
- * invalid plan): jobs that neither depend on another job nor are depended
- * on run as launches of the rectangle tiles, one per tile variant (packed
- * jobs before the persistent kernel, RLE-path jobs after it, once it has
- * encoded their source pages); the persistent kernel runs the rest. */
+ * invalid plan): the grouped tile launches plus the persistent kernel when
+ * the plan has work items for it. */
 MORPH_API int morph_batch_kernels(const void *host_plan);
 /* Test hook on a host plan (before it is copied to the device):
  * what = 0: set the wait limit to `value` ns (>= 1 ms; default 4 s);

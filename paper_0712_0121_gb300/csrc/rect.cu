@@ -128,7 +128,10 @@ int rect_plan(RectArgs &a, int op, int sw, int sh, int ox, int oy, int band_hint
     }
     auto smem_words = [&](const RectArgs &t) { return rle_src ? rle_rect_smem_words(t) : rect_smem_words(t); };
     const TilingOverride &ov = tiling_override();
-    const bool force_v = ov.vmode >= 0 && sh >= 4 && (ov.vmode == RV_VHGW || (ov.vmode == RV_CNT && sh <= RECT_CNT_SH));
+    // (the run-length-source tile has the counter mode only where the planner
+    // picks it itself: two stages, two words per thread)
+    const bool force_v = ov.vmode >= 0 && sh >= 4 &&
+                         (ov.vmode == RV_VHGW || (ov.vmode == RV_CNT && sh <= RECT_CNT_SH && !rle_src));
     if (force_v) a.vmode = ov.vmode;
     if (!nwt_hint) nwt_hint = ov.nwt;
     if (!threads_hint) threads_hint = ov.threads;

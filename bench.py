@@ -418,8 +418,10 @@ def run_config1(M, stream, reps):
 
 def run_uneven_batch(M, args, stream):
     """Uneven batch: seeded pages of four sizes, ink density U(1,30) %, each
-    with its own rectangle and op; per-page path and band from the autotuner;
-    one persistent launch (CUDA graph) vs a loop of per-page launches."""
+    with its own rectangle and op; per-page path and band from the autotuner
+    (tuned per page size); one batch launch (CUDA graph) vs the same
+    per-page launches captured in one CUDA graph, and vs a host loop of
+    them."""
     import torch
     from paper_0712_0121_gb300 import autotune, synth
     t0 = time.perf_counter()

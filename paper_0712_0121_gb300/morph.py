@@ -541,7 +541,7 @@ def abi_version() -> int:
 # ----------------------------------------------------------------- batch
 
 class Batch:
-    """A persistent batch launch over many packed pages (``morph_batch_*``).
+    """One batch launch over many packed pages (``morph_batch_*``).
 
     ``jobs``: list of dicts with keys ``op`` ("erode"/"dilate"/"open"/"close"
     or code, or "to_rle"), ``se`` ((se_w, se_h); not for "to_rle"), optional
@@ -550,7 +550,9 @@ class Batch:
     "to_rle"), optional ``depends_on`` (index of an earlier job) and
     ``tile_rows`` (row-band height of packed tiles).
     The plan is built on the host, copied to the device once, and every
-    :meth:`launch` is one kernel launch (graph-capturable)."""
+    :meth:`launch` is one call of ``morph_batch_launch`` (:attr:`kernels`
+    kernel launches: grouped tile launches and the persistent kernel;
+    graph-capturable)."""
 
     def __init__(self, jobs, tile_rows: int = 0, rle_runs_per_row: int = 0, device="cuda",
                  debug=None):

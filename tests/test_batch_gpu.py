@@ -158,3 +158,44 @@ def test_shared_encode_overflow_is_reported():
     for j in jobs:
         ref = oracle.apply(j["op"], img, 3, 3)
         assert np.array_equal(unpack_words(j["dst"].words, W), ref)
+
+
+def test_dependency_chains_across_grouped_and_persistent_jobs():
+    """Chains whose links run on different parts of the launch: packed jobs
+    grouped level by level (0, 1, 2), an RLE job reading a grouped job's
+    result, a packed job reading an RLE job's result (run by the persistent
+    kernel), and a conversion of a chain's last page to runs."""
+    rng_pages = [synth.text_page(640, 480, 9300 + k, 0.12, glyph=(4, 12, 6, 14), gap=(2, 6), ncols=2)[0]
+                 for k in range(2)]
+    a, b = rng_pages
+    P = lambda img: M.pack(img, 64)  # noqa: E731
+    E = lambda: M.Packed.empty(640, 480, 64)  # noqa: E731
+    src_a, src_b = P(a), P(b)
+    a1, a2, a3, a4 = E(), E(), E(), E()
+    b1, b2 = E(), E()
+    rle_out = M.Rle.empty(640, 480, 480 * 321)
+    jobs = [
+        dict(op="close", se=(15, 15), path="packed", src=src_a, dst=a1),                    # 0, level 0
+        dict(op="open", se=(3, 3), path="packed", src=a1, dst=a2, depends_on=0),             # 1, level 1
+        dict(op="dilate", se=(1, 15), path="packed", src=a2, dst=a3, depends_on=1),          # 2, level 2
+        dict(op="erode", se=(5, 5), path="rle", src=a3, dst=a4, depends_on=2),               # 3, persistent
+        dict(op="open", se=(7, 7), path="rle", src=src_b, dst=b1),                           # 4, persistent
+        dict(op="close", se=(3, 3), path="packed", src=b1, dst=b2, depends_on=4),            # 5, persistent
+        dict(op="to_rle", src=a4, dst=rle_out, depends_on=3),                                # 6, persistent
+    ]
+    bt = M.Batch(jobs)
+    assert bt.kernels >= 4  # three packed levels and the persistent kernel
+    for _ in range(2):  # a replay gives the same pages
+        bt.launch()
+        assert M.sync_status() == M.MORPH_OK
+        ra = a
+        for op, (sw, sh) in (("close", (15, 15)), ("open", (3, 3)), ("dilate", (1, 15)), ("erode", (5, 5))):
+            ra = oracle.apply(op, ra, sw, sh, mode="separable", threads=NCORES)
+        rb = oracle.apply("close", oracle.apply("open", b, 7, 7, mode="separable", threads=NCORES), 3, 3,
+                          mode="separable", threads=NCORES)
+        assert np.array_equal(unpack_words(a4.words, 640), ra)
+        assert np.array_equal(unpack_words(b2.words, 640), rb)
+        g_rp, g_runs = rle_out.to_numpy()
+        o_rp, o_runs = oracle.rle_encode(ra)
+        assert np.array_equal(g_rp, o_rp)
+        assert np.array_equal(g_runs.reshape(-1, 2), o_runs.reshape(-1, 2))

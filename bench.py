@@ -281,6 +281,7 @@ def time_launches(fn, steps, stream):
 PER_OP_SES = [(3, 3), (5, 5), (7, 7), (15, 15), (31, 31), (51, 51), (1, 51), (51, 1), (101, 1), (1, 61)]
 DENSITY_KINDS = ("blank", "text", "halftone", "noise")
 DENSITY_OPS = (("dilate", 101, 1), ("dilate", 1, 61), ("open", 5, 5))
+DENSITY_DISCS = (3, 12, 25)
 
 
 def median_ms(fn, reps, stream):
@@ -375,6 +376,23 @@ def run_density_sweep(M, peak, stream, reps, copies):
                         "frac": round(rb / (t_r * 1e-3) / 1e9 / peak, 3), "runs_out_per_row": round(runs_out / rows, 1),
                         "with_conversions_gpix_s": round(Wd * rows / ((t_r + t_enc + t_dec) * 1e-3) / 1e9, 1)},
             })
+            del pws, rws
+        # closing by discs (section "Experiments", circular masks): the
+        # packed path and the RLE path (runs in, runs out)
+        rec["disc_close"] = []
+        for r in DENSITY_DISCS:
+            disc = np.zeros((2 * r + 1, 2 * r + 1), np.uint8)
+            jj, ii = np.mgrid[0:2 * r + 1, 0:2 * r + 1]
+            disc[((ii - r) ** 2 + (jj - r) ** 2) <= r * r] = 1
+            pws = torch.empty(max(1, M.mask_workspace_size("close", dst, stack, disc, r, r)), dtype=torch.uint8,
+                              device="cuda")
+            t_p = median_ms(lambda: M.morph_mask("close", dst, stack, disc, r, r, workspace=pws), reps, stream)
+            rws = torch.empty(max(1, M.mask_workspace_size("close", b, a, disc, r, r)), dtype=torch.uint8,
+                              device="cuda")
+            t_r = median_ms(lambda: M.morph_mask("close", b, a, disc, r, r, workspace=rws), reps, stream)
+            rec["disc_close"].append({"r": r, "element_runs": 2 * r + 1,
+                                      "packed_ms": round(t_p, 4), "rle_ms": round(t_r, 4),
+                                      "runs_out_per_row": round(int(b.n_runs.item()) / rows, 1)})
             del pws, rws
         st = M.sync_status()
         if st != M.MORPH_OK:

@@ -178,7 +178,7 @@ MORPH_API morph_status morph_rle_rect_noalloc(int op, const morph_image *dst,
 
 /* ------------------------------------------------------- arbitrary masks --
  * Section "Morphology with Arbitrary Masks": erosion / dilation / opening /
- * closing of a packed image by an arbitrary structuring element.
+ * closing of a packed or RLE image by an arbitrary structuring element.
  *   mask: HOST memory, mask_h rows of mask_w bytes, row 0 first; a nonzero
  *         byte puts that pixel (i, j) in the element (read during the call
  *         only).  1 <= mask_w, mask_h <= 4096; at least one pixel; at most
@@ -188,14 +188,25 @@ MORPH_API morph_status morph_rle_rect_noalloc(int op, const morph_image *dst,
  *   E(x,y) = AND of src(x+i-ox, y+j-oy) over set (i,j) inside the image,
  *   D(x,y) = OR of src(x-i+ox, y-j+oy) over set (i,j) inside the image,
  *   open = D(E), close = E(D); a full mask gives exactly morph_rect.
- * Run at a time with doubling accumulation: doubling levels of the image up
- * to the longest run are built in the workspace, then every output word is
- * the AND of two level words per run.  src and dst packed (either word size),
- * same size, not overlapping.  Workspace (device, 256-byte aligned):
- * morph_mask_workspace_size() bytes (0 = none needed; that function returns
- * 0 also for invalid arguments, which morph_mask then reports).  Errors:
- * MORPH_EINVAL (arguments, RLE images, empty or too large element),
- * MORPH_ENOMEM (workspace too small), MORPH_ECUDA. */
+ * Packed images (either word size): run at a time with doubling
+ * accumulation — doubling levels of the image up to the longest run are
+ * built in the workspace, then every output word is the AND of two level
+ * words per run.
+ * RLE images (src and dst both RLE): run at a time on the runs — for each
+ * run of the element, every run of the image line it reaches (for an
+ * erosion, every gap between runs: the erosion is the complement of the
+ * dilation of the complement by the reflected element) is grown by the
+ * element run and painted into the output line, which is then encoded into
+ * runs; open / close encode their first stage into an intermediate RLE in the
+ * workspace (never full: it holds ceil(W/2) runs per line).  dst's capacity
+ * too small latches MORPH_ECAPACITY (read by morph_sync_status) and leaves
+ * its runs unwritten, as for the rectangles.
+ * src and dst the same size, not overlapping.  Workspace (device, 256-byte
+ * aligned): morph_mask_workspace_size() bytes (0 = none needed; that
+ * function returns 0 also for invalid arguments, which morph_mask then
+ * reports).  Errors: MORPH_EINVAL (arguments, one packed and one RLE image,
+ * empty or too large element), MORPH_ENOMEM (workspace too small),
+ * MORPH_ECUDA. */
 MORPH_API size_t morph_mask_workspace_size(int op, const morph_image *dst, const morph_image *src,
                                            const uint8_t *mask, int mask_w, int mask_h,
                                            int origin_x, int origin_y);
@@ -372,13 +383,13 @@ MORPH_API morph_status morph_run_length_hist(int64_t *black_hist, int64_t *white
  *    concurrently on the library's four auxiliary streams of the device,
  *    forked from and joined back into the caller's stream;
  *  - then one persistent kernel runs every other job (RLE-path jobs with a
- *    dependency or without a between-line pass, MORPH_TO_RLE jobs, packed
+ *    dependency or depended on, MORPH_TO_RLE jobs, packed
  *    jobs the tile cannot plan) and the bitmap -> RLE encodes of the
  *    source pages of RLE-path jobs;
- *  - then RLE-path jobs that neither depend on a job nor are depended on and
- *    have a between-line pass run as grouped launches of the run-length
- *    source tile, which read the persistent kernel's encodes (both stages of
- *    an opening or closing in one pass).
+ *  - then RLE-path jobs that neither depend on a job nor are depended on run
+ *    as grouped launches of the run-length source tile, which read the
+ *    persistent kernel's encodes (both stages of an opening or closing in
+ *    one pass).
  * morph_batch_kernels() returns the number of kernel launches of one call.
  *
  * Use: morph_batch_plan_bytes() -> a host buffer; morph_batch_plan_build()

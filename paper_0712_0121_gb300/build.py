@@ -22,7 +22,7 @@ BUILD = os.path.join(ROOT, "_build")
 
 CUDA_SOURCES = ["abi.cu", "packed.cu", "rle.cu", "batch.cu", "mask.cu", "noalloc.cu", "cc.cu", "transpose.cu", "skew.cu", "layout.cu",
                 "rect.cu", "rect_k1w2.cu", "rect_k1w4.cu", "rect_k2w2.cu", "rect_k2w4.cu",
-                "rle_rect_w2.cu", "rle_rect_w4.cu"]
+                "rle_rect_w2.cu", "rle_rect_w4.cu", "rle_mask.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-fvisibility=hidden",
               "-I" + INCLUDE, "-I" + CSRC]

@@ -370,17 +370,107 @@ morph_status check_mask_args(int op, const morph_image *dst, const morph_image *
     if (st) return st;
     if ((st = check_image(dst, "dst"))) return st;
     if (op < MORPH_ERODE || op > MORPH_CLOSE) return fail(MORPH_EINVAL, "op %d is not a morph_op", op);
-    if (!is_packed(src->fmt) || !is_packed(dst->fmt))
-        return fail(MORPH_EINVAL, "arbitrary masks take packed images");
+    if (is_packed(src->fmt) != is_packed(dst->fmt))
+        return fail(MORPH_EINVAL, "src and dst must both be packed or both be RLE");
     if (dst->width != src->width || dst->height != src->height)
         return fail(MORPH_EINVAL, "dst is %d x %d but src is %d x %d", dst->width, dst->height,
                     src->width, src->height);
-    if (overlap(packed_range(src), packed_range(dst))) return fail(MORPH_EINVAL, "dst overlaps src");
+    if (is_packed(src->fmt)) {
+        if (overlap(packed_range(src), packed_range(dst))) return fail(MORPH_EINVAL, "dst overlaps src");
+    } else {
+        const Range srp{(uintptr_t)src->row_ptr, (uintptr_t)(src->row_ptr + src->height + 1)};
+        const Range drp{(uintptr_t)dst->row_ptr, (uintptr_t)(dst->row_ptr + dst->height + 1)};
+        const Range dru{(uintptr_t)dst->runs, (uintptr_t)(dst->runs + 2 * dst->capacity_runs)};
+        const Range sru{(uintptr_t)src->runs, (uintptr_t)(src->runs + 2 * src->capacity_runs)};
+        if (overlap(srp, drp) || overlap(srp, dru) || overlap(sru, drp) || overlap(sru, dru))
+            return fail(MORPH_EINVAL, "dst overlaps src");
+    }
     if (!mask) return fail(MORPH_EINVAL, "mask is NULL");
     if (mw < 1 || mh < 1 || mw > MASK_MAX_SIDE || mh > MASK_MAX_SIDE)
         return fail(MORPH_EINVAL, "mask %d x %d outside 1..%d", mw, mh, MASK_MAX_SIDE);
     if (ox < 0 || ox >= mw || oy < 0 || oy >= mh)
         return fail(MORPH_EINVAL, "origin (%d, %d) outside the %d x %d mask", ox, oy, mw, mh);
+    return MORPH_OK;
+}
+
+// Runs of the element as painted intervals of one RLE stage (rle_mask.cu):
+// a dilation paints each run [s, e) of line y - j + oy grown to
+// [s + i0 - ox, e + i1 - 1 - ox); an erosion paints each gap of line
+// y + j - oy grown to [s - (i1 - 1) + ox, e - i0 + ox) and complements.
+morph_status rle_mask_runs(const uint8_t *mask, int mw, int mh, int ox, int oy, bool erode,
+                           RleMaskArgs &a) {
+    int n = 0;
+    for (int j = 0; j < mh; ++j) {
+        const uint8_t *row = mask + (size_t)j * mw;
+        for (int i = 0; i < mw;) {
+            if (!row[i]) { ++i; continue; }
+            const int i0 = i;
+            while (i < mw && row[i]) ++i;
+            const int i1 = i;
+            if (n == MASK_MAX_RUNS)
+                return fail(MORPH_EINVAL, "structuring element has more than %d horizontal runs",
+                            MASK_MAX_RUNS);
+            RleMaskRun &u = a.runs[n++];
+            if (erode) {
+                u.dy = j - oy;
+                u.lo = ox - (i1 - 1);
+                u.hi = ox - i0;
+            } else {
+                u.dy = oy - j;
+                u.lo = i0 - ox;
+                u.hi = i1 - 1 - ox;
+            }
+        }
+    }
+    if (n == 0) return fail(MORPH_EINVAL, "structuring element has no pixel");
+    a.nruns = n;
+    return MORPH_OK;
+}
+
+// RLE images: each stage paints into the bitmap scratch and encodes it
+// (open / close encode the first stage into the intermediate RLE).
+morph_status run_rle_mask(int op, const morph_image *dst, const morph_image *src, const uint8_t *mask,
+                          int mw, int mh, int ox, int oy, void *ws, size_t ws_bytes, cudaStream_t s) {
+    static thread_local RleMaskArgs a;  // 12 KB: kept off the stack
+    const int W = src->width, H = src->height, nw = (W + 31) / 32;
+    const RleWs L = rle_ws(op, W, H);
+    if (!ws || ws_bytes < L.total)
+        return fail(MORPH_ENOMEM, "the mask operation needs %zu bytes of workspace, got %zu", L.total,
+                    ws ? ws_bytes : (size_t)0);
+    if ((uintptr_t)ws % 256) return fail(MORPH_EINVAL, "workspace is not 256-byte aligned");
+    char *base = (char *)ws;
+    int32_t *counts = (int32_t *)(base + L.counts);
+    uint32_t *bmp = (uint32_t *)(base + L.bmp);
+    int *st = device_status_ptr();
+    const bool two = op == MORPH_OPEN || op == MORPH_CLOSE;
+    const bool erode0 = op == MORPH_ERODE || op == MORPH_OPEN;
+    morph_status ms = rle_mask_runs(mask, mw, mh, ox, oy, erode0, a);
+    if (ms) return ms;
+    a.row_ptr = src->row_ptr;
+    a.runs_u16 = src->runs;
+    a.W = W;
+    a.H = H;
+    a.dst = bmp;
+    a.dstride = nw;
+    a.nw = nw;
+    a.erode = erode0;
+    cudaError_t e = launch_rle_mask_stage(a, s);
+    if (e == cudaSuccess && !two) e = launch_rle_from_bitmap(bmp, nw, W, H, rle_out(dst), counts, st, s);
+    if (e == cudaSuccess && two) {
+        // the intermediate holds up to ceil(W / 2) runs per line: never full
+        const RleOut tmp{(int32_t *)(base + L.tmp_rowptr), (uint16_t *)(base + L.tmp_runs), L.tmp_capacity,
+                         (int64_t *)(base + L.tmp_nruns)};
+        e = launch_rle_from_bitmap(bmp, nw, W, H, tmp, counts, st, s);
+        if (e == cudaSuccess) {
+            if ((ms = rle_mask_runs(mask, mw, mh, ox, oy, !erode0, a))) return ms;
+            a.row_ptr = tmp.row_ptr;
+            a.runs_u16 = tmp.runs;
+            a.erode = !erode0;
+            e = launch_rle_mask_stage(a, s);
+        }
+        if (e == cudaSuccess) e = launch_rle_from_bitmap(bmp, nw, W, H, rle_out(dst), counts, st, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "RLE mask morphology launch");
     return MORPH_OK;
 }
 
@@ -567,6 +657,11 @@ size_t morph_mask_workspace_size(int op, const morph_image *dst, const morph_ima
                                  const uint8_t *mask, int mask_w, int mask_h, int origin_x,
                                  int origin_y) {
     if (check_mask_args(op, dst, src, mask, mask_w, mask_h, origin_x, origin_y)) return 0;
+    if (src->fmt == MORPH_RLE) {
+        static thread_local RleMaskArgs r;
+        if (rle_mask_runs(mask, mask_w, mask_h, origin_x, origin_y, true, r)) return 0;
+        return rle_ws(op, src->width, src->height).total;
+    }
     static thread_local MaskArgs a;
     if (mask_runs(mask, mask_w, mask_h, origin_x, origin_y, false, a)) return 0;
     return mask_ws_bytes(op, src->width, src->height, a.nlev);
@@ -577,6 +672,9 @@ morph_status morph_mask(int op, const morph_image *dst, const morph_image *src, 
                         size_t workspace_bytes, void *stream) {
     morph_status st = check_mask_args(op, dst, src, mask, mask_w, mask_h, origin_x, origin_y);
     if (st) return st;
+    if (src->fmt == MORPH_RLE)
+        return run_rle_mask(op, dst, src, mask, mask_w, mask_h, origin_x, origin_y, workspace,
+                            workspace_bytes, (cudaStream_t)stream);
     static thread_local MaskArgs a;  // 8 KB: kept off the stack
     const int W = src->width, H = src->height, nwv = (W + 31) / 32;
     // stages: erosion by the element (AND) or dilation by the reflected one (OR)

@@ -116,7 +116,8 @@ struct BatchHeader {
     int64_t jobs_off, items_off, plan_bytes;
     int64_t ws_ctrl_bytes, ws_bytes;
     int64_t wait_limit_ns;
-    int32_t n_groups, pad0;
+    int32_t n_groups;
+    int32_t kb_after_groups;  // a persistent-kernel job reads a grouped packed job's result
     int64_t groups_off;
 };
 
@@ -485,10 +486,11 @@ void add_to_group(std::vector<GroupPlan> &G, int rle, int level, const RectArgs 
 
 morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per_row,
                    std::vector<BatchJob> &J, std::vector<BatchItem> &I, int64_t &ws_ctrl,
-                   int64_t &ws_total, int &smem, std::vector<GroupPlan> &G) {
+                   int64_t &ws_total, int &smem, std::vector<GroupPlan> &G, int *kb_after_groups = nullptr) {
     J.assign(n, BatchJob{});
     G.clear();
     smem = 0;
+    if (kb_after_groups) *kb_after_groups = 0;
     // jobs another job depends on stay inside the persistent kernel
     std::vector<char> depended(n, 0);
     for (int j = 0; j < n; ++j)
@@ -526,6 +528,7 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
         if (b.dep >= 0 && glevel[b.dep] >= 0) {
             b.dep = -1;
             b.dep_phase = 0;
+            if (kb_after_groups) *kb_after_groups = 1;
         }
         b.src_job = j;
         if (q.op == MORPH_TO_RLE) {
@@ -650,11 +653,11 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
             // encode phases instead of encoding again.  Only jobs without a
             // user dependency share, and only encoders whose A stays intact
             // (a two-stage run pass writes its second stage into A).
-            // windows taller than a row, independent jobs: the run-length-
-            // source tile after the persistent kernel (which only encodes)
+            // independent jobs: the run-length-source tile after the
+            // persistent kernel (which only encodes their source pages)
             bool fused = false;
             RectArgs fra;
-            if (c.sh > 1 && independent) {
+            if (independent) {
                 memset(&fra, 0, sizeof(fra));
                 fra.dst = (uint32_t *)d.words;
                 fra.dstride = d.stride_words * (Bd / 32);
@@ -667,7 +670,7 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
                     fused = true;
                 }
             }
-            const bool a_rewritten = b.nst == 2 && c.sh == 1;
+            const bool a_rewritten = b.nst == 2 && c.sh == 1 && !fused;
             int enc = -1;
             if (q.depends_on < 0) {
                 const SrcKey key{s.words, s.stride_words, s.fmt, W, H};
@@ -804,12 +807,16 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
 // Streams the batch launch forks its tile groups onto (per device, created
 // once, never destroyed), with the events of the fork and of the join.  The
 // launch sequence holds the device's mutex, so one set serves every caller.
-constexpr int AUX_STREAMS = 4;
+// Streams 0 .. AUX_PACKED - 1 run the packed groups, the others the RLE
+// groups, so that the two kinds overlap (the packed tiles are bound by
+// integer logic, the run-length-source tiles by latency).
+constexpr int AUX_STREAMS = 8;
+constexpr int AUX_PACKED = 4;
 struct AuxStreams {
     std::mutex mu;
     bool made = false;
     cudaStream_t st[AUX_STREAMS];
-    cudaEvent_t fork, kb_done, join[AUX_STREAMS];
+    cudaEvent_t fork, kb_done, join[AUX_STREAMS], level[AUX_PACKED];
 };
 AuxStreams *aux_streams(int dev, cudaError_t &e) {
     static AuxStreams a[64];
@@ -827,6 +834,7 @@ cudaError_t make_aux(AuxStreams &a) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.kb_done, cudaEventDisableTiming);
     for (int k = 0; k < AUX_STREAMS && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&a.join[k], cudaEventDisableTiming);
+    for (int k = 0; k < AUX_PACKED && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&a.level[k], cudaEventDisableTiming);
     if (e == cudaSuccess) a.made = true;
     return e;
 }
@@ -872,11 +880,12 @@ morph_status morph_batch_plan_build(void *host_plan, size_t plan_bytes, const mo
     std::vector<BatchItem> I;
     std::vector<GroupPlan> G;
     int64_t ctrl, total;
-    int smem;
-    morph_status st = build(jobs, n_jobs, tile_rows, rle_runs_per_row, J, I, ctrl, total, smem, G);
+    int smem, kb_after = 0;
+    morph_status st = build(jobs, n_jobs, tile_rows, rle_runs_per_row, J, I, ctrl, total, smem, G, &kb_after);
     if (st != MORPH_OK) return st;
     BatchHeader h;
     memset(&h, 0, sizeof(h));
+    h.kb_after_groups = kb_after;
     h.magic = PLAN_MAGIC;
     h.n_jobs = n_jobs;
     h.n_items = (int32_t)I.size();
@@ -1003,9 +1012,13 @@ morph_status morph_batch_launch(const void *dev_plan, const void *host_plan, voi
         else ++npk;
     }
     // Tile groups run on the device's auxiliary streams, forked from and
-    // joined back into the caller's stream: the packed groups of each level
-    // together, then the persistent kernel, then the RLE groups (they read
-    // its encodes).
+    // joined back into the caller's stream, ordered only by what they read:
+    //  - packed groups on streams 0 .. AUX_PACKED - 1, level by level (the
+    //    packed streams meet at an event barrier between levels);
+    //  - the persistent kernel on the caller's stream, at once, or after the
+    //    last packed level when one of its jobs reads a grouped job's result;
+    //  - RLE groups on the other streams once the persistent kernel has
+    //    encoded their sources.
     int dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     AuxStreams *ax = nullptr;
@@ -1016,40 +1029,33 @@ morph_status morph_batch_launch(const void *dev_plan, const void *host_plan, voi
         lk = std::unique_lock<std::mutex>(ax->mu);
         e = make_aux(*ax);
     }
-    int used = 0;
-    auto aux_for = [&](int i) {
-        const int k = i % AUX_STREAMS;
-        if (k + 1 > used) used = k + 1;
-        return ax->st[k];
-    };
-    // fork the auxiliary streams from the caller's stream, and join them back
-    auto fork = [&](cudaEvent_t ev) {
-        cudaError_t r = cudaEventRecord(ev, s);
-        for (int k = 0; r == cudaSuccess && k < AUX_STREAMS; ++k) r = cudaStreamWaitEvent(ax->st[k], ev, 0);
-        return r;
-    };
-    auto join = [&]() {
+    const int np = npk > 0 ? AUX_PACKED : 0;                    // packed streams in use
+    const int nr = nrl > 0 ? AUX_STREAMS - AUX_PACKED : 0;      // RLE streams in use
+    // every packed stream waits for every other one's last launch
+    auto packed_barrier = [&]() {
         cudaError_t r = cudaSuccess;
-        for (int k = 0; r == cudaSuccess && k < AUX_STREAMS; ++k) {
-            r = cudaEventRecord(ax->join[k], ax->st[k]);
-            if (r == cudaSuccess) r = cudaStreamWaitEvent(s, ax->join[k], 0);
-        }
+        for (int k = 0; r == cudaSuccess && k < np; ++k) r = cudaEventRecord(ax->level[k], ax->st[k]);
+        for (int k = 0; r == cudaSuccess && k < np; ++k)
+            for (int q = 0; r == cudaSuccess && q < np; ++q)
+                if (q != k) r = cudaStreamWaitEvent(ax->st[k], ax->level[q], 0);
         return r;
     };
-    // packed groups level by level (a level's jobs read the level below);
-    // the persistent kernel follows the last level
+    if (ax && e == cudaSuccess) {
+        e = cudaEventRecord(ax->fork, s);
+        for (int k = 0; e == cudaSuccess && k < np; ++k) e = cudaStreamWaitEvent(ax->st[k], ax->fork, 0);
+    }
     int maxlevel = -1;
     for (int k = 0; k < h->n_groups; ++k)
         if (!groups[k].rle && groups[k].ctas > 0 && groups[k].level > maxlevel) maxlevel = groups[k].level;
     int gi = 0;
     for (int lv = 0; e == cudaSuccess && lv <= maxlevel; ++lv) {
-        e = fork(ax->fork);
+        if (lv > 0) e = packed_barrier();
         for (int k = 0; e == cudaSuccess && k < h->n_groups; ++k) {
             const TileGroup &g = groups[k];
             if (g.rle || g.ctas < 1 || g.level != lv) continue;
             const RectJobs mj{reinterpret_cast<const RectArgs *>(dp + g.jobs_off),
                               reinterpret_cast<const int *>(dp + g.starts_off), g.njobs, g.ctas, (size_t)g.smem};
-            e = launch_rect(g.proto, aux_for(gi++), &mj);
+            e = launch_rect(g.proto, ax->st[gi++ % AUX_PACKED], &mj);
             if (e != cudaSuccess) {
                 set_error("batch launch: packed group %d (stages %d, %d words, modes %d/%d/%d, %d threads, %d "
                           "CTAs, %lld bytes shared): %s", k, g.proto.nst, g.proto.nwt, g.proto.vmode,
@@ -1058,9 +1064,13 @@ morph_status morph_batch_launch(const void *dev_plan, const void *host_plan, voi
                 return MORPH_ECUDA;
             }
         }
-        if (e == cudaSuccess) e = join();
     }
     if (h->n_items > 0) {
+        if (np > 0 && h->kb_after_groups && e == cudaSuccess) {
+            // the persistent kernel reads results of the packed groups
+            for (int k = 0; e == cudaSuccess && k < np; ++k) e = cudaEventRecord(ax->level[k], ax->st[k]);
+            for (int k = 0; e == cudaSuccess && k < np; ++k) e = cudaStreamWaitEvent(s, ax->level[k], 0);
+        }
         if (e == cudaSuccess) e = cudaMemsetAsync(workspace, 0, (size_t)h->ws_ctrl_bytes, s);
         if (e == cudaSuccess) {
             k_batch<<<n_ctas, BATCH_THREADS, smem, s>>>(dp, (uint8_t *)workspace, device_status_ptr());
@@ -1068,14 +1078,19 @@ morph_status morph_batch_launch(const void *dev_plan, const void *host_plan, voi
         }
     }
     // RLE groups read the encodes of the persistent kernel: fork after it
-    if (nrl > 0 && e == cudaSuccess) e = fork(ax->kb_done);
+    if (nr > 0 && e == cudaSuccess) {
+        e = cudaEventRecord(ax->kb_done, s);
+        for (int k = AUX_PACKED; e == cudaSuccess && k < AUX_STREAMS; ++k)
+            e = cudaStreamWaitEvent(ax->st[k], ax->kb_done, 0);
+    }
+    int ri = 0;
     for (int k = 0; e == cudaSuccess && k < h->n_groups; ++k) {
         const TileGroup &g = groups[k];
         if (!g.rle || g.ctas < 1) continue;
         const RleJobs mj{reinterpret_cast<const RleJob *>(dp + g.jobs_off),
                          reinterpret_cast<const int *>(dp + g.starts_off), (const uint8_t *)workspace, g.njobs,
                          g.ctas, (size_t)g.smem};
-        e = launch_rle_rect_tile(g.proto, RleSrc{}, aux_for(gi++), &mj);
+        e = launch_rle_rect_tile(g.proto, RleSrc{}, ax->st[AUX_PACKED + ri++ % (AUX_STREAMS - AUX_PACKED)], &mj);
         if (e != cudaSuccess) {
             set_error("batch launch: RLE group %d (stages %d, %d words, modes %d/%d/%d, %d threads, %d CTAs, "
                       "%lld bytes shared): %s", k, g.proto.nst, g.proto.nwt, g.proto.vmode, g.proto.hmode,
@@ -1083,8 +1098,15 @@ morph_status morph_batch_launch(const void *dev_plan, const void *host_plan, voi
             return MORPH_ECUDA;
         }
     }
-    if (nrl > 0 && e == cudaSuccess) e = join();
-    (void)used;
+    // join every stream that was forked back into the caller's stream
+    for (int k = 0; e == cudaSuccess && k < np; ++k) {
+        e = cudaEventRecord(ax->join[k], ax->st[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ax->join[k], 0);
+    }
+    for (int k = AUX_PACKED; e == cudaSuccess && k < AUX_PACKED + nr; ++k) {
+        e = cudaEventRecord(ax->join[k], ax->st[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ax->join[k], 0);
+    }
     if (e != cudaSuccess) {
         set_error("batch launch: %s", cudaGetErrorString(e));
         return MORPH_ECUDA;

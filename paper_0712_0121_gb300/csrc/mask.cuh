@@ -32,4 +32,26 @@ __host__ __device__ inline int mask_pad_words(int nlev) { return ((1 << nlev) - 
 size_t mask_levels_bytes(int W, int H, int nlev);
 cudaError_t launch_mask_stage(const MaskArgs &a, cudaStream_t s);
 
+// One stage on an RLE image (rle_mask.cu): for each element run, source
+// line y + dy, every interval [a, b) of that line (its runs, or for an
+// erosion its gaps) paints [a + lo, b + hi) of output line y.
+struct RleMaskRun {
+    int32_t dy, lo, hi;
+};
+struct RleMaskArgs {
+    const int32_t *row_ptr;   // source RLE
+    const uint16_t *runs_u16;
+    int W, H;
+    uint32_t *dst;            // packed output lines (u32 words)
+    int64_t dstride;
+    int nw;                   // u32 words per line: (W + 31) / 32
+    int erode;                // 1: paint the gaps, output the complement
+    int nruns;
+    RleMaskRun runs[MASK_MAX_RUNS];
+};
+// Warps (output lines) per CTA for lines of nw words; 0 when one line does
+// not fit the CTA's shared memory.
+int rle_mask_warps(int nw);
+cudaError_t launch_rle_mask_stage(const RleMaskArgs &a, cudaStream_t s);
+
 }  // namespace morph

@@ -53,7 +53,10 @@ __global__ void __launch_bounds__(256, 2) k_rect(const RectArgs a, const RectArg
         sby = local / gx;
     }
     __syncthreads();
-    rect_tile<NST, NWT, VM, HM, HALO>(sj, sbx, sby, sm);
+    // the job's plan in registers: read through shared memory, every field
+    // would be loaded again after each of the tile's barriers
+    const RectArgs la = sj;
+    rect_tile<NST, NWT, VM, HM, HALO>(la, sbx, sby, sm);
 }
 
 template <int NST, int NWT, int VM, int HM, int HALO>

@@ -30,7 +30,10 @@ __global__ void __launch_bounds__(256, 2) k_rle_rect(const RectArgs a, const Rle
         sbx = blockIdx.x - starts[j];
     }
     __syncthreads();
-    rle_rect_tile<NST, NWT, VM, HM, HALO>(sj, ss, sbx, sm);
+    // the job's plan in registers (see k_rect)
+    const RectArgs la = sj;
+    const RleSrc ls = ss;
+    rle_rect_tile<NST, NWT, VM, HM, HALO>(la, ls, sbx, sm);
 }
 
 template <int NST, int NWT, int VM, int HM, int HALO>
@@ -99,12 +102,13 @@ cudaError_t rle_rect_launch_nw(const RectArgs &a, const RleSrc &src, cudaStream_
         }
     }
     switch (a.vmode) {
+    case RV_NONE: return rle_rect_launch_h2<NWT, RV_NONE>(a, src, s, mj);  // sh == 1
     case RV_W3: return rle_rect_launch_h2<NWT, RV_W3>(a, src, s, mj);
     case RV_VHGW: return rle_rect_launch_h2<NWT, RV_VHGW>(a, src, s, mj);
     case RV_CNT:
         if constexpr (NWT == 2) return rle_rect_launch_h2<NWT, RV_CNT>(a, src, s, mj);
         return cudaErrorInvalidValue;
-    default: return cudaErrorInvalidValue;  // sh == 1: the row pass on the runs
+    default: return cudaErrorInvalidValue;
     }
 }
 

@@ -335,12 +335,13 @@ def _mask_bytes(mask) -> np.ndarray:
     return np.ascontiguousarray(m != 0, dtype=np.uint8)
 
 
-def morph_mask(op, dst: "Packed", src: "Packed", mask, origin_x=None, origin_y=None,
+def morph_mask(op, dst, src, mask, origin_x=None, origin_y=None,
                workspace: torch.Tensor | None = None, stream=None) -> None:
-    """Erode / dilate / open / close packed ``src`` into ``dst`` by an
-    arbitrary structuring element ``mask`` (2D array, nonzero = in the
-    element).  Origin defaults to the centre (mask_w // 2, mask_h // 2).  A
-    workspace is allocated here when none is given."""
+    """Erode / dilate / open / close ``src`` into ``dst`` (both
+    :class:`Packed` or both :class:`Rle`) by an arbitrary structuring element
+    ``mask`` (2D array, nonzero = in the element).  Origin defaults to the
+    centre (mask_w // 2, mask_h // 2).  A workspace is allocated here when
+    none is given."""
     m = _mask_bytes(mask)
     mh, mw = m.shape
     ox = mw // 2 if origin_x is None else origin_x
@@ -349,7 +350,8 @@ def morph_mask(op, dst: "Packed", src: "Packed", mask, origin_x=None, origin_y=N
     if workspace is None:
         n = mask_workspace_size(opc, dst, src, m, ox, oy)
         if n:
-            workspace = torch.empty(n, dtype=torch.uint8, device=src.words.device)
+            dev = src.row_ptr.device if src.fmt == RLE else src.words.device
+            workspace = torch.empty(n, dtype=torch.uint8, device=dev)
     wp, wn = _ws_args(workspace)
     _check(_lib.morph_mask(opc, ctypes.byref(dst.desc()), ctypes.byref(src.desc()),
                            m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), mw, mh, ox, oy, wp, wn,

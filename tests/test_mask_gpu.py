@@ -1,8 +1,9 @@
 """Arbitrary structuring elements (section "Morphology with Arbitrary
-Masks") on the packed path, through the C ABI, bit for bit against the
-oracle's pixel-at-a-time definition: random elements with gaps and origins
-outside the element, discs, full rectangles (which must equal the rectangle
-path), ragged sizes, both word formats, wide elements, and the errors."""
+Masks") on the packed path and on RLE images, through the C ABI, bit for bit
+against the oracle's pixel-at-a-time definition: random elements with gaps
+and origins outside the element, discs, full rectangles (which must equal the
+rectangle path), ragged sizes, both word formats, wide elements, runs
+touching the line ends, and the errors."""
 import ctypes
 
 import numpy as np
@@ -136,3 +137,88 @@ def test_errors():
                         None, 0, None)
     assert st == M.MORPH_ENOMEM
     assert M.sync_status() == M.MORPH_OK
+
+
+# ------------------------------------------------------------- RLE images
+
+def rle_mask_op(op, img, mask, ox, oy, capacity=None):
+    H, W = img.shape
+    rp, runs = oracle.rle_encode(img)
+    src = M.Rle.from_numpy(rp, runs, W)
+    dst = M.Rle.empty(W, H, capacity if capacity is not None else H * ((W + 1) // 2))
+    M.morph_mask(op, dst, src, mask, ox, oy)
+    return dst
+
+
+def check_rle(op, img, mask, ox, oy):
+    dst = rle_mask_op(op, img, mask, ox, oy)
+    assert M.sync_status() == M.MORPH_OK
+    g_rp, g_runs = dst.to_numpy()
+    o_rp, o_runs = oracle.rle_encode(oracle.apply_mask(op, img, mask, ox, oy, threads=NCORES))
+    assert np.array_equal(g_rp, o_rp), (op, mask.shape, ox, oy, img.shape)
+    assert np.array_equal(g_runs.reshape(-1, 2), np.asarray(o_runs).reshape(-1, 2)), (op, mask.shape, ox, oy)
+    assert int(dst.n_runs.item()) == o_rp[-1]
+
+
+@pytest.mark.parametrize("op", OPS)
+@pytest.mark.parametrize("W,H", [(1, 1), (33, 7), (64, 40), (100, 129), (517, 61)])
+def test_rle_random_masks_ragged_sizes(op, W, H):
+    rng = np.random.default_rng(W * 11 + H)
+    img = synth.random_bits((H, W), 6100 + W + H, 0.6 if op in ("erode", "open") else 0.2)
+    for k in range(4):
+        m = rand_mask(rng, 1 + (k * 5) % 9, 1 + (k * 7) % 13, 0.5)
+        ox, oy = int(rng.integers(m.shape[1])), int(rng.integers(m.shape[0]))
+        check_rle(op, img, m, ox, oy)
+
+
+@pytest.mark.parametrize("op", OPS)
+def test_rle_discs_on_a_text_page(op):
+    img = synth.text_page(700, 520, 92, 0.15, glyph=(5, 12, 7, 14), gap=(2, 6), ncols=2)[0]
+    for r in (1, 3, 9, 14):
+        check_rle(op, img, oracle.disc_mask(r), r, r)
+
+
+def test_rle_runs_at_the_line_ends_and_origin_outside():
+    img = synth.random_bits((60, 97), 78, 0.5)
+    img[:, 0] = 1
+    img[:, -1] = 1            # runs that touch both ends of every line
+    img[10] = 1               # a full line
+    img[20] = 0               # an empty line
+    ring = np.ones((5, 5), np.uint8)
+    ring[1:4, 1:4] = 0        # the origin (2, 2) is not in the element
+    bar = np.ones((1, 201), np.uint8)   # wider than the image
+    tall = np.ones((81, 1), np.uint8)   # taller than the image
+    for op in OPS:
+        check_rle(op, img, ring, 2, 2)
+        check_rle(op, img, bar, 100, 0)
+        check_rle(op, img, tall, 0, 40)
+
+
+def test_rle_full_rectangle_mask_equals_the_rectangle_path():
+    img = synth.text_page(300, 257, 79, 0.2, glyph=(4, 9, 5, 11), gap=(1, 5))[0]
+    rp, runs = oracle.rle_encode(img)
+    src = M.Rle.from_numpy(rp, runs, 300)
+    for op in OPS:
+        for sw, sh, ox, oy in [(3, 3, 1, 1), (7, 2, 0, 1), (15, 15, 14, 0)]:
+            a = rle_mask_op(op, img, np.ones((sh, sw), np.uint8), ox, oy)
+            b = M.Rle.empty(300, 257, 257 * 151)
+            M.morph_rect(op, b, src, sw, sh, ox, oy)
+            assert M.sync_status() == M.MORPH_OK
+            (arp, aruns), (brp, bruns) = a.to_numpy(), b.to_numpy()
+            assert np.array_equal(arp, brp) and np.array_equal(aruns, bruns), (op, sw, sh)
+
+
+def test_rle_config2_page_disc_open():
+    img, _ = synth.config2_page()
+    check_rle("open", img, oracle.disc_mask(6), 6, 6)
+
+
+def test_rle_mask_capacity_and_format_errors():
+    img = synth.random_bits((30, 64), 5, 0.5)
+    dst = rle_mask_op("dilate", img, np.ones((1, 3), np.uint8), 1, 0, capacity=3)
+    assert M.sync_status() == M.MORPH_ECAPACITY
+    rp, runs = oracle.rle_encode(img)
+    src = M.Rle.from_numpy(rp, runs, 64)
+    with pytest.raises(M.MorphError):
+        M.morph_mask("erode", M.Packed.empty(64, 30, 64), src, np.ones((3, 3), np.uint8))  # mixed formats
+    del dst

@@ -212,13 +212,14 @@ def whole_job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
 
 
 # The dominant kernel of a step (the largest share of the step's launch
-# list): the grouped launch of the two-stage rectangle tile whose vertical
-# passes use bit-sliced run counters, which runs the packed open / close jobs
-# of these rectangles (their van Herk / Gil-Werman rings for two stages do
-# not fit two CTAs per SM).
+# list): the two-stage rectangle tile whose vertical passes use bit-sliced
+# run counters, which runs the packed open / close jobs of these rectangles
+# (their van Herk / Gil-Werman rings for two stages do not fit two CTAs per
+# SM); one grouped launch per counter width.
 DOMINANT_SES = ((15, 15), (31, 31), (51, 51))
-DOMINANT_KERNEL = ("k_rect<2 stages, 2 words/thread, counter vertical, log horizontal>: one grouped "
-                   "launch of the packed open/close jobs by 15x15, 31x31, 51x51")
+DOMINANT_KERNEL = ("k_rect<2 stages, 2 words/thread, counter vertical (4, 5, 6 bit planes), log horizontal>: "
+                   "the grouped launches of the packed open/close jobs by 15x15, 31x31, 51x51 (one per "
+                   "plane count, side by side on the batch's packed streams)")
 # Sources that kernel and its planner are built from.
 DOMINANT_SOURCES = ("rect_tile.cuh", "rect_kernels.cuh", "rect.cu", "rect_k2w2.cu", "counters.cuh",
                     "morph_internal.cuh", "batch.cu")

@@ -21,14 +21,13 @@ int round_up(int v, int m) { return (v + m - 1) / m * m; }
 constexpr int RECT_MAX_GROUPS = 16;
 
 // Optional override of the tiling for tuning runs: MORPH_RECT_TILING =
-// "nwt,threads,band,prefetch_rows,vmode" (0 keeps the default of the first
-// four fields, -1 of the last; the L2 row prefetch is off by default).  Read
-// once.
+// "nwt,threads,band,vmode" (0 keeps the default of the first three fields,
+// -1 of the last).  Read once.
 struct TilingOverride {
-    int nwt = 0, threads = 0, band = 0, pf = -1, vmode = -1;
+    int nwt = 0, threads = 0, band = 0, vmode = -1;
     TilingOverride() {
         const char *e = getenv("MORPH_RECT_TILING");
-        if (e) sscanf(e, "%d,%d,%d,%d,%d", &nwt, &threads, &band, &pf, &vmode);
+        if (e) sscanf(e, "%d,%d,%d,%d", &nwt, &threads, &band, &vmode);
     }
 };
 const TilingOverride &tiling_override() {
@@ -128,10 +127,7 @@ int rect_plan(RectArgs &a, int op, int sw, int sh, int ox, int oy, int band_hint
     }
     auto smem_words = [&](const RectArgs &t) { return rle_src ? rle_rect_smem_words(t) : rect_smem_words(t); };
     const TilingOverride &ov = tiling_override();
-    // (the run-length-source tile has the counter mode only where the planner
-    // picks it itself: two stages, two words per thread)
-    const bool force_v = ov.vmode >= 0 && sh >= 4 &&
-                         (ov.vmode == RV_VHGW || (ov.vmode == RV_CNT && sh <= RECT_CNT_SH && !rle_src));
+    const bool force_v = ov.vmode >= 0 && sh >= 4 && (ov.vmode == RV_VHGW || (ov.vmode == RV_CNT && sh <= RECT_CNT_SH));
     if (force_v) a.vmode = ov.vmode;
     if (!nwt_hint) nwt_hint = ov.nwt;
     if (!threads_hint) threads_hint = ov.threads;
@@ -158,6 +154,12 @@ int rect_plan(RectArgs &a, int op, int sw, int sh, int ox, int oy, int band_hint
         tile(a, nwt_hint ? nwt_hint : 2, threads_hint ? threads_hint : 256);
         done = true;
     }
+    // two-stage counters: as many bit planes as sh has bits (the 4- and
+    // 5-plane variants are built for two words per thread)
+    if (rv_cnt(a.vmode) && a.nst == 2 && a.nwt == 2) a.vmode = sh < 16 ? RV_CNT4 : (sh < 32 ? RV_CNT5 : RV_CNT);
+    // the run-length-source tile has counters for two stages and two words
+    // per thread only (a forced tiling may ask for others)
+    if (rle_src && rv_cnt(a.vmode) && (a.nst != 2 || a.nwt != 2)) return -1;
     if (!done) tile(a, 2, 128);
     // windows too tall for the rings of even the smallest tiling: the caller
     // falls back to the bit-sliced counter tile (O(log sh) state per word)
@@ -172,16 +174,11 @@ int rect_plan(RectArgs &a, int op, int sw, int sh, int ox, int oy, int band_hint
     if (band_hint <= 0 && band > 1024) band = 1024;
     a.band_auto = band_hint <= 0;
     set_band(a, band);
-    // L2 prefetch of whole rows by one thread per group: rows of one strip,
-    // 16-byte aligned, sized down to a multiple of 16 bytes
-    a.pf_rows = 0;
-    a.pf_bytes = 0;
-    if (a.nstrips == 1 && (uintptr_t)a.src % 16 == 0 && a.sstride % 4 == 0) {
-        a.pf_bytes = (uint32_t)(a.nw_valid * 4) & ~15u;
-        if (a.pf_bytes) a.pf_rows = ov.pf > 0 ? ov.pf : 0;  // measured slower on by default
-    }
     a.nw_full = a.W / 32;
     a.vec16 = ((uintptr_t)a.dst % 16 == 0) && (a.dstride % 4 == 0);
+    // one strip whose 8-word tasks all lie inside the written words: every
+    // task stores two aligned 16-byte vectors, no per-word checks
+    a.vec_tasks = a.vec16 && a.nstrips == 1 && a.halo_words == 0 && a.row_words <= a.nw_cover;
     // the horizontal tasks of a chunk must fit the threads' task slots (the
     // most groups a launch may give the CTA)
     {

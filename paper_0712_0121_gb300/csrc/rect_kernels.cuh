@@ -124,6 +124,12 @@ cudaError_t rect_launch_nw(const RectArgs &a, cudaStream_t s, const RectJobs *mj
     case RV_NONE: return rect_launch_h<NST, NWT, RV_NONE>(a, s, mj);
     case RV_W3: return rect_launch_h<NST, NWT, RV_W3>(a, s, mj);
     case RV_CNT: return rect_launch_h<NST, NWT, RV_CNT>(a, s, mj);
+    case RV_CNT4:
+        if constexpr (NST == 2 && NWT == 2) return rect_launch_h<NST, NWT, RV_CNT4>(a, s, mj);
+        return cudaErrorInvalidValue;
+    case RV_CNT5:
+        if constexpr (NST == 2 && NWT == 2) return rect_launch_h<NST, NWT, RV_CNT5>(a, s, mj);
+        return cudaErrorInvalidValue;
     default: return rect_launch_h<NST, NWT, RV_VHGW>(a, s, mj);
     }
 }

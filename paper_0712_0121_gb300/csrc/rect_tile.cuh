@@ -57,7 +57,11 @@
 
 namespace morph {
 
-enum RectVMode { RV_NONE = 0, RV_W3 = 1, RV_VHGW = 2, RV_CNT = 3 };
+// RV_CNT: counters of 6 bit planes (sh < 64); RV_CNT4 / RV_CNT5: 4 or 5
+// planes for sh < 16 / sh < 32 (two stages, two words per thread only)
+enum RectVMode { RV_NONE = 0, RV_W3 = 1, RV_VHGW = 2, RV_CNT = 3, RV_CNT4 = 4, RV_CNT5 = 5 };
+__host__ __device__ constexpr bool rv_cnt(int vm) { return vm == RV_CNT || vm == RV_CNT4 || vm == RV_CNT5; }
+__host__ __device__ constexpr int rv_planes(int vm) { return vm == RV_CNT4 ? 4 : (vm == RV_CNT5 ? 5 : 6); }
 enum RectHMode { RH_NONE = 0, RH_D1 = 1, RH_D2 = 2, RH_LOG = 3 };
 
 struct RectArgs {
@@ -92,8 +96,7 @@ struct RectArgs {
     int ktasks;           // horizontal tasks per thread and chunk (at most RECT_KT)
     int nw_full;          // words holding 32 pixels: W / 32
     int vec16;            // dst 16-byte aligned and dstride a multiple of 4 words
-    int pf_rows;          // rows between a row's L2 prefetch and its use (0: none)
-    uint32_t pf_bytes;    // bytes prefetched per row (a multiple of 16)
+    int vec_tasks;        // every horizontal task stores 8 whole aligned words inside the row
 };
 
 constexpr int RECT_RB = 8;  // bands are whole multiples of this many rows
@@ -235,11 +238,16 @@ __device__ __forceinline__ void shifted(const uint32_t (&A)[NWT + 2 * HALO], int
 }
 
 // Horizontal erosion of one row: window [x - L, x + R] of the stage input
-// held in `win` (shared memory, the thread's own words at `own`).
+// held in `win` (shared memory, the thread's own words at `own`), XORed with
+// inm (the complement of a dilation or of the next stage's input, folded
+// into the last logic operation).
 template <int NWT, int HM, int HALO>
-__device__ __forceinline__ void rect_hpass(const uint32_t *own, int L, int R, int m, uint32_t (&out)[NWT]) {
+__device__ __forceinline__ void rect_hpass(const uint32_t *own, int L, int R, int m, uint32_t inm,
+                                           uint32_t (&out)[NWT]) {
     if constexpr (HM == RH_NONE) {
         lds_own<NWT>(own, out);
+#pragma unroll
+        for (int t = 0; t < NWT; ++t) out[t] ^= inm;
     } else if constexpr (HM == RH_D1 || HM == RH_D2) {
         uint32_t v[NWT + 2];
         lds_win<NWT, 1>(own, v);
@@ -254,7 +262,7 @@ __device__ __forceinline__ void rect_hpass(const uint32_t *own, int L, int R, in
                 const int r2 = R < 2 ? R : 2, l2 = L < 2 ? L : 2;
                 e &= __funnelshift_r(c, nx, r2) & __funnelshift_l(pv, c, l2);
             }
-            out[t] = e;
+            out[t] = e ^ inm;
         }
     } else {
         constexpr int NWIN = NWT + 2 * HALO;
@@ -279,7 +287,7 @@ __device__ __forceinline__ void rect_hpass(const uint32_t *own, int L, int R, in
         shifted<NWT, HALO>(A, -L, lo);
         shifted<NWT, HALO>(A, R + 1 - (1 << m), hi);
 #pragma unroll
-        for (int t = 0; t < NWT; ++t) out[t] = lo[t] & hi[t];
+        for (int t = 0; t < NWT; ++t) out[t] = (lo[t] & hi[t]) ^ inm;
     }
 }
 
@@ -294,9 +302,10 @@ struct RectV {
     uint32_t *ring;    // VHGW: this thread's column of the ring, entries rstride words apart
     uint32_t *rp;      // VHGW: entry j
     int rstride;
-    ColCounter<6> cnt[NWT];  // CNT: run counters
-    uint32_t eqm[6];         // CNT: per plane, ones where that bit of sh is 0
-    int K;                   // CNT: bit length of sh
+    static constexpr int KP = rv_planes(VM);
+    ColCounter<KP> cnt[NWT];  // CNT: run counters
+    uint32_t eqm[KP];         // CNT: per plane, ones where that bit of sh is 0
+    int K;                    // CNT: bit length of sh
 
     __device__ __forceinline__ void init(uint32_t *ring_base, int tid, int threads, int sh) {
 #pragma unroll
@@ -305,13 +314,13 @@ struct RectV {
             p2[t] = ONES;
         }
         keep2 = sh == 3 ? 0u : ONES;
-        if constexpr (VM == RV_CNT) {
+        if constexpr (rv_cnt(VM)) {
 #pragma unroll
             for (int t = 0; t < NWT; ++t) cnt[t].reset();
             K = 0;
             for (int v = sh; v; v >>= 1) ++K;
 #pragma unroll
-            for (int k = 0; k < 6; ++k) eqm[k] = ((sh >> k) & 1) ? 0u : ONES;
+            for (int k = 0; k < KP; ++k) eqm[k] = ((sh >> k) & 1) ? 0u : ONES;
         }
         j = 0;
         ring = ring_base + tid * NWT;
@@ -340,7 +349,7 @@ struct RectV {
                 p2[t] = g[t] | keep2;
                 g[t] = in[t];
             }
-        } else if constexpr (VM == RV_CNT) {
+        } else if constexpr (rv_cnt(VM)) {
 #pragma unroll
             for (int t = 0; t < NWT; ++t) out[t] = cnt[t].push(in[t], K, eqm);
         } else {
@@ -427,12 +436,14 @@ struct RectTasks {
 
 // Horizontal pass of one chunk of exchanged rows as tasks of RECT_NWH words
 // of one row.  LAST: the task's words of output row u0 + i of its group's
-// band go to the destination (complemented by inm_out, padding bits 0);
-// otherwise they go into `yb` at the same slot position.
+// band go to the destination (complemented by inm, padding bits 0);
+// otherwise they go, complemented by inm, into `yb` at the same slot
+// position.  With the plan's vec_tasks every task is 8 whole, 16-byte
+// aligned words inside the row: its store needs no per-word checks.
 template <int HM, int HALO, bool LAST>
 __device__ __forceinline__ void rect_htasks(const RectArgs &a, const RectTasks &tasks, const uint32_t *xb,
                                             uint32_t *yb, int u0, int L, int R, int bx, int strip0,
-                                            int strip_end, uint32_t inm_out, int row_words) {
+                                            int strip_end, uint32_t inm, int row_words) {
     constexpr int NWH = RECT_NWH;
     const int groups = a.groups, band = a.band, H = a.H;
     const int64_t dstride = a.dstride;
@@ -441,28 +452,24 @@ __device__ __forceinline__ void rect_htasks(const RectArgs &a, const RectTasks &
     for (int tk = threadIdx.x; tk < tasks.total; tk += blockDim.x) {
         const int off = i * row_words + gq * a.slot_words + a.pad + sg * NWH;
         uint32_t h[NWH];
-        rect_hpass<NWH, HM, HALO>(xb + off, L, R, a.m, h);
+        rect_hpass<NWH, HM, HALO>(xb + off, L, R, a.m, inm, h);
         if constexpr (LAST) {
             const int y = (bx * groups + gq) * band + u0 + i;
             if (y < H) {
                 const int ws = strip0 - a.halo_words + sg * NWH;  // first word of the task
                 uint32_t *p = a.dst + (int64_t)y * dstride + ws;
-                uint32_t o[NWH];
-#pragma unroll
-                for (int t = 0; t < NWH; ++t) o[t] = h[t] ^ inm_out;
                 if (ws + NWH > a.nw_full) {
                     // the row's last words: padding bits and words past the
-                    // pixels are written 0 (logic only, so the warp stays on
-                    // one path)
+                    // pixels are written 0
 #pragma unroll
-                    for (int t = 0; t < NWH; ++t) o[t] &= word_mask(ws + t, a.W);
+                    for (int t = 0; t < NWH; ++t) h[t] &= word_mask(ws + t, a.W);
                 }
-                if (a.vec16 && (ws & 3) == 0 && ws >= strip0 && ws + NWH <= strip_end) {
-                    RectVec<NWH>::st(p, o);
+                if (a.vec_tasks || (a.vec16 && (ws & 3) == 0 && ws >= strip0 && ws + NWH <= strip_end)) {
+                    RectVec<NWH>::st(p, h);
                 } else {
 #pragma unroll
                     for (int t = 0; t < NWH; ++t)
-                        if (ws + t >= strip0 && ws + t < strip_end) p[t] = o[t];
+                        if (ws + t >= strip0 && ws + t < strip_end) p[t] = h[t];
                 }
             }
         } else {
@@ -535,8 +542,6 @@ __device__ __forceinline__ void rect_tile(const RectArgs &a, int bx, int by, uin
     const bool vec_path = a.vec_rows != 0;
     (void)all_ld;
     (void)all_st;
-    // one thread per group prefetches whole rows into L2, pf_rows ahead
-    const bool pf_lead = act && lt == 0 && a.pf_rows > 0;
     const uint32_t inm_in = a.inv_in ? ONES : 0u, inm_out = a.inv_out ? ONES : 0u;
 
     // shared memory: exchange sets (the stage-1 vertical result; for two
@@ -647,14 +652,6 @@ __device__ __forceinline__ void rect_tile(const RectArgs &a, int bx, int by, uin
                         for (int t = 0; t < NWT; ++t) q[i][t] = 0u;
                     }
                 }
-                if (pf_lead) {
-                    const int rp = rc + i + a.pf_rows;
-                    if (rp >= 0 && rp < H) {
-                        const uint32_t *pp = a.src + (int64_t)rp * sstride;
-                        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(pp), "r"(a.pf_bytes)
-                                     : "memory");
-                    }
-                }
                 lp += sstride;
                 v1.push(in, o, sh);
                 if constexpr (XCH) {
@@ -679,9 +676,12 @@ __device__ __forceinline__ void rect_tile(const RectArgs &a, int bx, int by, uin
         // (rect_htasks): the last stage stores rows u0 + i of its group's
         // band, stage 1 of two writes its rows into `yb` for the stage-2
         // vertical pass.
+        // (stage 1 of two hands its rows back complemented: the stage-2
+        // vertical pass erodes the complement)
         auto htasks = [&](const uint32_t *xb, uint32_t *yb, int u0, int L, int R, auto last_flag) {
-            rect_htasks<HM, HALO, decltype(last_flag)::value>(a, tasks, xb, yb, u0, L, R, bx, strip0, strip_end,
-                                                              inm_out, row_words);
+            constexpr bool LST = decltype(last_flag)::value;
+            rect_htasks<HM, HALO, LST>(a, tasks, xb, yb, u0, L, R, bx, strip0, strip_end, LST ? inm_out : ONES,
+                                       row_words);
         };
 
         // Two stages: the stage-2 vertical pass of a chunk of stage-1 rows
@@ -700,7 +700,7 @@ __device__ __forceinline__ void rect_tile(const RectArgs &a, int bx, int by, uin
                 const int y1 = y10 + i;
                 const uint32_t fill2 = (f2free || (y1 >= 0 && y1 < H)) ? 0u : ONES;
 #pragma unroll
-                for (int t = 0; t < NWT; ++t) in2[t] = ~h[t] | nmw[t] | fill2;
+                for (int t = 0; t < NWT; ++t) in2[t] = h[t] | nmw[t] | fill2;  // h: complemented already
                 v2.push(in2, o2, sh);
                 if (act && w2) RV::st(xo + i * row_words, o2);
             }

@@ -108,6 +108,12 @@ cudaError_t rle_rect_launch_nw(const RectArgs &a, const RleSrc &src, cudaStream_
     case RV_CNT:
         if constexpr (NWT == 2) return rle_rect_launch_h2<NWT, RV_CNT>(a, src, s, mj);
         return cudaErrorInvalidValue;
+    case RV_CNT4:
+        if constexpr (NWT == 2) return rle_rect_launch_h2<NWT, RV_CNT4>(a, src, s, mj);
+        return cudaErrorInvalidValue;
+    case RV_CNT5:
+        if constexpr (NWT == 2) return rle_rect_launch_h2<NWT, RV_CNT5>(a, src, s, mj);
+        return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
     }
 }

@@ -212,17 +212,18 @@ def whole_job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
 
 
 # The dominant kernel of a step (the largest share of the step's launch
-# list): the two-stage rectangle tile whose vertical passes use bit-sliced
-# run counters, which runs the packed open / close jobs of these rectangles
-# (their van Herk / Gil-Werman rings for two stages do not fit two CTAs per
-# SM); one grouped launch per counter width.
-DOMINANT_SES = ((15, 15), (31, 31), (51, 51))
-DOMINANT_KERNEL = ("k_rect<2 stages, 2 words/thread, counter vertical (4, 5, 6 bit planes), log horizontal>: "
-                   "the grouped launches of the packed open/close jobs by 15x15, 31x31, 51x51 (one per "
-                   "plane count, side by side on the batch's packed streams)")
+# list, profiles/bench_step_letter300_launch_list.md): the run-length-source
+# tile's grouped launch that runs the RLE open / close jobs of these
+# rectangles (two stages, van Herk / Gil-Werman rings, doubling second
+# horizontal pass).
+DOMINANT_PATH = "rle"
+DOMINANT_SES = ((7, 7), (15, 15))
+DOMINANT_KERNEL = ("k_rle_rect<2 stages, 2 words/thread, ring vertical, log horizontal>: the grouped "
+                   "launch of the RLE open/close jobs by 7x7 and 15x15 (runs in, bitmap out), timed "
+                   "without the persistent encode kernel")
 # Sources that kernel and its planner are built from.
-DOMINANT_SOURCES = ("rect_tile.cuh", "rect_kernels.cuh", "rect.cu", "rect_k2w2.cu", "counters.cuh",
-                    "morph_internal.cuh", "batch.cu")
+DOMINANT_SOURCES = ("rle_rect.cuh", "rle_rect_kernels.cuh", "rle_rect_w2.cu", "rect_tile.cuh", "rect.cu",
+                    "rle_tile.cuh", "counters.cuh", "morph_internal.cuh", "batch.cu")
 
 
 def csrc_digest():
@@ -895,11 +896,15 @@ def run_ours(args):
     bytes_launch -= B * max(0, rle_per_page - 1) * encode_bytes(mean_runs_in)
     step_achieved = bytes_launch / (ms * 1e-3) / 1e9
 
-    # the dominant kernel alone: a batch of just its jobs is one grouped
-    # launch of that tile (forked onto an auxiliary stream and joined back,
-    # so events on this stream bracket it), timed like the steps
-    dom = [j for j in jobs if j["path"] == "packed" and tuple(j["se"]) in DOMINANT_SES]
+    # the dominant kernel alone: a batch of just its jobs; one full launch
+    # leaves the sources' encodes in the workspace, then the tile group runs
+    # by itself (forked onto an auxiliary stream and joined back, so events
+    # on this stream bracket it), timed like the steps
+    dom = [j for j in jobs if j["path"] == DOMINANT_PATH and tuple(j["se"]) in DOMINANT_SES]
     bdom = M.Batch(dom, rle_runs_per_row=args.rle_runs_per_row)
+    bdom.launch(stream=stream)
+    torch.cuda.synchronize()
+    bdom.debug(2, 1)  # the tile groups alone
     gdom = bdom.capture()
     for _ in range(3):
         gdom.replay()
@@ -908,7 +913,13 @@ def run_ours(args):
     st = M.sync_status()
     if st != M.MORPH_OK:
         raise RuntimeError("device status %d after the dominant-kernel launches" % st)
-    dom_bytes = sum(alg_bytes("packed", 0, 0) for _ in dom)
+    page_bytes = H * NW * 8
+    if DOMINANT_PATH == "rle":
+        # runs and row offsets of the page read, the bitmap written
+        dom_unit = 4 * mean_runs_in + 4 * (H + 1) + page_bytes
+    else:
+        dom_unit = 2 * page_bytes
+    dom_bytes = len(dom) * dom_unit
     dom_kernels = bdom.kernels
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     del bdom, gdom
@@ -1035,11 +1046,11 @@ def run_ours(args):
         "packed_gpix_s": round(sub["packed"], 1), "rle_gpix_s": round(sub["rle"], 1),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": profile_traffic("k_rect_open_close_cnt_letter_dram.md", B),
+                     "traffic": profile_traffic("k_rle_rect_open_close_letter_dram.md", B),
                      "kernel": DOMINANT_KERNEL, "peak_source": peak_src,
                      "page_ops_per_launch": len(dom), "launches": dom_kernels,
                      "alg_bytes_per_launch": int(dom_bytes), "ms_per_launch": round(dom_ms, 4),
-                     "alg_bytes_per_page_op": 2 * H * NW * 8},
+                     "alg_bytes_per_page_op": int(dom_unit)},
         "step_roofline": {"alg_bytes_per_step": int(bytes_launch), "achieved": round(step_achieved, 1),
                           "unit": "GB/s", "frac": round(step_achieved / peak, 4),
                           "kernels_per_step": batch.kernels},

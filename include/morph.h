@@ -449,12 +449,17 @@ MORPH_API int morph_batch_items(const void *host_plan);
  * invalid plan): the grouped tile launches plus the persistent kernel when
  * the plan has work items for it. */
 MORPH_API int morph_batch_kernels(const void *host_plan);
-/* Test hook on a host plan (before it is copied to the device):
+/* Test and timing hooks on a host plan (what = 0 and 1 before the plan is
+ * copied to the device; what = 2 at any time — the launch reads it there):
  * what = 0: set the wait limit to `value` ns (>= 1 ms; default 4 s);
  * what = 1: add `value` to the item count that the second phase of the first
  *           multi-phase (RLE-path) job waits for, so that its wait runs out —
  *           used to check that MORPH_ETIMEOUT is reported and the device stays
- *           usable. */
+ *           usable;
+ * what = 2: value != 0 launches the tile groups alone, without the
+ *           persistent kernel — to time the groups once an earlier launch of
+ *           the same plan has left its encodes in the workspace (the RLE
+ *           groups read them); value 0 restores the full launch. */
 MORPH_API morph_status morph_batch_plan_debug(void *host_plan, int what, long long value);
 /* n_ctas <= 0: as many CTAs as fit on the device at once. */
 MORPH_API morph_status morph_batch_launch(const void *dev_plan, const void *host_plan,

@@ -118,6 +118,8 @@ struct BatchHeader {
     int64_t wait_limit_ns;
     int32_t n_groups;
     int32_t kb_after_groups;  // a persistent-kernel job reads a grouped packed job's result
+    int32_t groups_only;      // timing hook: launch the tile groups alone (morph_batch_plan_debug 2)
+    int32_t pad0;
     int64_t groups_off;
 };
 
@@ -927,7 +929,7 @@ morph_status morph_batch_plan_build(void *host_plan, size_t plan_bytes, const mo
 int morph_batch_kernels(const void *host_plan) {
     const BatchHeader *h = (const BatchHeader *)host_plan;
     if (!h || h->magic != PLAN_MAGIC) return -1;
-    return h->n_groups + (h->n_items > 0 ? 1 : 0);
+    return h->n_groups + (h->n_items > 0 && !h->groups_only ? 1 : 0);
 }
 
 size_t morph_batch_workspace_size(const void *host_plan) {
@@ -956,6 +958,10 @@ morph_status morph_batch_plan_debug(void *host_plan, int what, long long value) 
             }
         set_error("no job with more than one phase");
         return MORPH_EINVAL;
+    }
+    if (what == 2) {
+        h->groups_only = value != 0;
+        return MORPH_OK;
     }
     set_error("unknown debug request %d", what);
     return MORPH_EINVAL;
@@ -1065,7 +1071,7 @@ morph_status morph_batch_launch(const void *dev_plan, const void *host_plan, voi
             }
         }
     }
-    if (h->n_items > 0) {
+    if (h->n_items > 0 && !h->groups_only) {
         if (np > 0 && h->kb_after_groups && e == cudaSuccess) {
             // the persistent kernel reads results of the packed groups
             for (int k = 0; e == cudaSuccess && k < np; ++k) e = cudaEventRecord(ax->level[k], ax->st[k]);

@@ -591,6 +591,10 @@ class Batch:
         self.n_items = int(_lib.morph_batch_items(hp))
         self.n_jobs = n
 
+    def debug(self, what: int, value: int) -> None:
+        """``morph_batch_plan_debug`` on the host plan (test and timing hooks)."""
+        _check(_lib.morph_batch_plan_debug(self.host_plan.ctypes.data, what, value))
+
     @property
     def kernels(self) -> int:
         """Kernel launches one :meth:`launch` makes."""

@@ -199,3 +199,26 @@ def test_dependency_chains_across_grouped_and_persistent_jobs():
         o_rp, o_runs = oracle.rle_encode(ra)
         assert np.array_equal(g_rp, o_rp)
         assert np.array_equal(g_runs.reshape(-1, 2), o_runs.reshape(-1, 2))
+
+
+def test_groups_only_launch_reuses_the_encodes():
+    """The timing hook (morph_batch_plan_debug 2) launches the tile groups
+    without the persistent kernel: after one full launch the RLE groups read
+    the encodes left in the workspace and write the same pages."""
+    specs = [(640, 480, "open", (7, 7), "rle", 0.12), (640, 480, "close", (15, 15), "rle", 0.12),
+             (640, 480, "open", (31, 31), "packed", 0.12)]
+    jobs, imgs = make_jobs(specs)
+    b = M.Batch(jobs)
+    full = b.kernels
+    b.launch()
+    assert M.sync_status() == M.MORPH_OK
+    check_all(jobs, imgs)
+    for j in jobs:
+        j["dst"].words.fill_(-1)
+    b.debug(2, 1)
+    assert b.kernels == full - 1
+    b.launch()
+    assert M.sync_status() == M.MORPH_OK
+    check_all(jobs, imgs)
+    b.debug(2, 0)
+    assert b.kernels == full

@@ -15,6 +15,11 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU and the built CUDA library")
+    # a fresh checkout: compile the library first (nvcc cross-compiles
+    # without a GPU; up-to-date builds return at once), so that the CPU tests
+    # of the ABI and the GPU tests find it
+    from paper_0712_0121_gb300 import build
+    build.build_all()
 
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")

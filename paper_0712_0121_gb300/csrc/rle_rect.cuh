@@ -126,7 +126,12 @@ __device__ __forceinline__ void rle_rect_tile(const RectArgs &a, const RleSrc &s
         // an encode that overflowed its buffer (reported by the status
         // latch) leaves offsets past the runs: never read beyond them
         const int q1 = (int64_t)rp[RB] < src.cap ? rp[RB] : (int)src.cap;
-        int row = 0;
+        // the chunk's row boundaries in registers: a run's row is the number
+        // of boundaries at or below it (offsets never decrease; empty rows
+        // are skipped), no walk through shared memory
+        int bnd[RB - 1];
+#pragma unroll
+        for (int i = 0; i < RB - 1; ++i) bnd[i] = rp[i + 1];
         for (int qb = q0 + lt; qb < q1; qb += 4 * tpr) {
             uint32_t pr[4];
 #pragma unroll
@@ -138,7 +143,9 @@ __device__ __forceinline__ void rle_rect_tile(const RectArgs &a, const RleSrc &s
             for (int e = 0; e < 4; ++e) {
                 const int q = qb + e * tpr;
                 if (q < q1) {
-                    while (rp[row + 1] <= q) ++row;
+                    int row = 0;
+#pragma unroll
+                    for (int i = 0; i < RB - 1; ++i) row += q >= bnd[i] ? 1 : 0;
                     int s2, e2;
                     run_interval(pr[e], src.op1, s2, e2);
                     s2 = s2 < 0 ? 0 : s2;

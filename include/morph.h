@@ -380,8 +380,10 @@ MORPH_API morph_status morph_run_length_hist(int64_t *black_hist, int64_t *white
  *    a job, run as grouped launches of the rectangle tile: one launch per
  *    tile variant and dependency level, over a device table of the level's
  *    jobs of that variant; the levels run in order, the launches of a level
- *    concurrently on the library's four auxiliary streams of the device,
- *    forked from and joined back into the caller's stream;
+ *    concurrently on the library's auxiliary streams of the device, forked
+ *    from and joined back into the caller's stream (a plan with at most one
+ *    group per level and at most one RLE group runs in stream order on the
+ *    caller's stream);
  *  - then one persistent kernel runs every other job (RLE-path jobs with a
  *    dependency or depended on, MORPH_TO_RLE jobs, packed
  *    jobs the tile cannot plan) and the bitmap -> RLE encodes of the

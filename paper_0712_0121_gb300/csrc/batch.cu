@@ -1030,13 +1030,28 @@ morph_status morph_batch_launch(const void *dev_plan, const void *host_plan, voi
     AuxStreams *ax = nullptr;
     if (e == cudaSuccess) ax = aux_streams(dev, e);
     if (e == cudaSuccess && npk + nrl == 0) ax = nullptr;
+    // a plan with at most one group per level and at most one RLE group (a
+    // single request's chain of jobs, say) has nothing to overlap: it runs in
+    // stream order on the caller's stream, without the fork, the level
+    // barriers and the join (dozens of event calls per launch)
+    {
+        int per_level[64] = {}, maxper = 0;
+        bool deep = false;
+        for (int k = 0; k < h->n_groups; ++k) {
+            if (groups[k].rle || groups[k].ctas < 1) continue;
+            if (groups[k].level >= 64) { deep = true; continue; }
+            const int c = ++per_level[groups[k].level];
+            if (c > maxper) maxper = c;
+        }
+        if (!deep && maxper <= 1 && nrl <= 1) ax = nullptr;
+    }
     std::unique_lock<std::mutex> lk;
     if (ax) {
         lk = std::unique_lock<std::mutex>(ax->mu);
         e = make_aux(*ax);
     }
-    const int np = npk > 0 ? AUX_PACKED : 0;                    // packed streams in use
-    const int nr = nrl > 0 ? AUX_STREAMS - AUX_PACKED : 0;      // RLE streams in use
+    const int np = ax && npk > 0 ? AUX_PACKED : 0;                  // packed streams in use
+    const int nr = ax && nrl > 0 ? AUX_STREAMS - AUX_PACKED : 0;    // RLE streams in use
     // every packed stream waits for every other one's last launch
     auto packed_barrier = [&]() {
         cudaError_t r = cudaSuccess;
@@ -1055,13 +1070,13 @@ morph_status morph_batch_launch(const void *dev_plan, const void *host_plan, voi
         if (!groups[k].rle && groups[k].ctas > 0 && groups[k].level > maxlevel) maxlevel = groups[k].level;
     int gi = 0;
     for (int lv = 0; e == cudaSuccess && lv <= maxlevel; ++lv) {
-        if (lv > 0) e = packed_barrier();
+        if (lv > 0 && ax) e = packed_barrier();
         for (int k = 0; e == cudaSuccess && k < h->n_groups; ++k) {
             const TileGroup &g = groups[k];
             if (g.rle || g.ctas < 1 || g.level != lv) continue;
             const RectJobs mj{reinterpret_cast<const RectArgs *>(dp + g.jobs_off),
                               reinterpret_cast<const int *>(dp + g.starts_off), g.njobs, g.ctas, (size_t)g.smem};
-            e = launch_rect(g.proto, ax->st[gi++ % AUX_PACKED], &mj);
+            e = launch_rect(g.proto, ax ? ax->st[gi++ % AUX_PACKED] : s, &mj);
             if (e != cudaSuccess) {
                 set_error("batch launch: packed group %d (stages %d, %d words, modes %d/%d/%d, %d threads, %d "
                           "CTAs, %lld bytes shared): %s", k, g.proto.nst, g.proto.nwt, g.proto.vmode,
@@ -1096,7 +1111,8 @@ morph_status morph_batch_launch(const void *dev_plan, const void *host_plan, voi
         const RleJobs mj{reinterpret_cast<const RleJob *>(dp + g.jobs_off),
                          reinterpret_cast<const int *>(dp + g.starts_off), (const uint8_t *)workspace, g.njobs,
                          g.ctas, (size_t)g.smem};
-        e = launch_rle_rect_tile(g.proto, RleSrc{}, ax->st[AUX_PACKED + ri++ % (AUX_STREAMS - AUX_PACKED)], &mj);
+        e = launch_rle_rect_tile(g.proto, RleSrc{}, ax ? ax->st[AUX_PACKED + ri++ % (AUX_STREAMS - AUX_PACKED)] : s,
+                                 &mj);
         if (e != cudaSuccess) {
             set_error("batch launch: RLE group %d (stages %d, %d words, modes %d/%d/%d, %d threads, %d CTAs, "
                       "%lld bytes shared): %s", k, g.proto.nst, g.proto.nwt, g.proto.vmode, g.proto.hmode,

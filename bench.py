@@ -161,7 +161,6 @@ def make_pages(n, seed_base=0):
 NW = (W + 63) // 64  # 64-bit words per row
 
 
-D2H_STREAMS = 1  # streams for the device->host result copies (1 to 4 measured alike)
 
 
 def build_jobs(M, srcs, paths):
@@ -960,19 +959,20 @@ def run_ours(args):
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
 
-    # end to end through the same API with host buffers
+    # end to end through the C ABI with host buffers: morph_batch_launch_host
+    # copies the step's pages in from pinned host memory, runs the batch and
+    # copies every result back, on one stream
     host_in = torch.empty((B, H, NW), dtype=torch.int64, pin_memory=True)
     host_in.copy_(dev_in)
     host_out = torch.empty((n_jobs, H, NW), dtype=torch.int64, pin_memory=True)
     e2e_steps = max(2, args.steps // 2)
+    batch.launch_host(host_in, dev_in, host_out, dev_out, stream=stream)  # warm-up
     torch.cuda.synchronize()
     s_ev, e_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2e_t = []
     for _ in range(e2e_steps):
         s_ev.record(stream)
-        dev_in.copy_(host_in, non_blocking=True)
-        graph.replay()
-        host_out.copy_(dev_out, non_blocking=True)
+        batch.launch_host(host_in, dev_in, host_out, dev_out, stream=stream)
         e_ev.record(stream)
         e_ev.synchronize()
         e2e_t.append(s_ev.elapsed_time(e_ev))
@@ -980,56 +980,38 @@ def run_ours(args):
     h2d = host_in.numel() * 8
     d2h = host_out.numel() * 8
 
-    # The same steps pipelined the way a serving host runs them: two sets of
-    # device buffers (each with its own batch plan), the host->device copy of
-    # step k+1 and the device->host read of step k's results on copy streams
-    # while step k+1's launch runs.  Every step still copies its inputs from
+    # The same calls pipelined the way a serving host runs them: two sets of
+    # device buffers (each with its own batch plan) and host result buffers,
+    # consecutive steps' calls on two streams, so that one step's copies run
+    # while the other's kernels do.  Every step still copies its inputs from
     # pinned host memory and reads all its results back.
     dev_in2 = torch.empty_like(dev_in)
     srcs2 = [M.Packed(dev_in2[k], W) for k in range(B)]
     jobs2, dev_out2 = build_jobs(M, srcs2, ("packed", "rle"))
     batch2 = M.Batch(jobs2, rle_runs_per_row=args.rle_runs_per_row)
-    bufs = [(dev_in, dev_out, batch), (dev_in2, dev_out2, batch2)]
-    s_h2d, s_cmp = torch.cuda.Stream(), torch.cuda.Stream()
-    s_d2h = [torch.cuda.Stream() for _ in range(D2H_STREAMS)]
-    ev = {name: [torch.cuda.Event(), torch.cuda.Event()] for name in ("h2d", "cmp")}
-    ev["d2h"] = [[torch.cuda.Event() for _ in range(D2H_STREAMS)] for _ in range(2)]
-    parts = np.array_split(np.arange(n_jobs), D2H_STREAMS)
+    host_out2 = torch.empty(host_out.shape, dtype=host_out.dtype, pin_memory=True)
+    bufs = [(dev_in, dev_out, batch, host_out), (dev_in2, dev_out2, batch2, host_out2)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
 
     def pipelined_steps(n):
         for k in range(n):
-            b = k % 2
-            din, dout, bat = bufs[b]
-            s_h2d.wait_event(ev["cmp"][b])        # the launch that read din is done
-            with torch.cuda.stream(s_h2d):
-                din.copy_(host_in, non_blocking=True)
-            ev["h2d"][b].record(s_h2d)
-            s_cmp.wait_event(ev["h2d"][b])
-            for e in ev["d2h"][b]:
-                s_cmp.wait_event(e)               # dout has been read back
-            bat.launch(stream=s_cmp)
-            ev["cmp"][b].record(s_cmp)
-            # the results leave in D2H_STREAMS pieces on as many streams
-            for q, idx in enumerate(parts):
-                s_d2h[q].wait_event(ev["cmp"][b])
-                with torch.cuda.stream(s_d2h[q]):
-                    host_out[idx[0]:idx[-1] + 1].copy_(dout[idx[0]:idx[-1] + 1], non_blocking=True)
-                ev["d2h"][b][q].record(s_d2h[q])
+            din, dout, bat, hout = bufs[k % 2]
+            bat.launch_host(host_in, din, hout, dout, stream=streams[k % 2])
 
     pipelined_steps(2)  # warm-up of the second plan and the streams
     torch.cuda.synchronize()
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    p0.record(s_h2d)
+    p0.record(streams[0])
+    streams[1].wait_event(p0)
     pipelined_steps(e2e_steps)
-    for q in range(D2H_STREAMS):
-        s_h2d.wait_stream(s_d2h[q])
-    p1.record(s_h2d)
+    streams[0].wait_stream(streams[1])
+    p1.record(streams[0])
     p1.synchronize()
     e2e_ms = p0.elapsed_time(p1) / e2e_steps
     st = M.sync_status()
     if st != M.MORPH_OK:
         raise RuntimeError("device status %d after the end-to-end steps" % st)
-    del batch2, jobs2, dev_out2, dev_in2, srcs2
+    del batch2, jobs2, dev_out2, dev_in2, srcs2, host_out2
     e2e_value = pix_step_rank * world / (e2e_ms * 1e-3) / 1e9
 
     line = {
@@ -1056,7 +1038,8 @@ def run_ours(args):
                           "kernels_per_step": batch.kernels},
         "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 3),
-                "steps": e2e_steps, "pipelined": "copies of neighbouring steps overlap the launch",
+                "steps": e2e_steps, "api": "morph_batch_launch_host (copy in, batch, copy out; C ABI)",
+                "pipelined": "calls of neighbouring steps on two streams: copies overlap kernels",
                 "unpipelined_ms_per_step": round(e2e_serial_ms, 3),
                 "unpipelined_value": round(pix_step_rank * world / (e2e_serial_ms * 1e-3) / 1e9, 2)},
         "gpu_launches": args.steps * batch.kernels,

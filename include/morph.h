@@ -468,6 +468,23 @@ MORPH_API morph_status morph_batch_launch(const void *dev_plan, const void *host
                                           void *workspace, size_t workspace_bytes, int n_ctas,
                                           void *stream);
 
+/* The batch between host buffers: copies in_bytes from host memory h_in to
+ * device memory d_in, runs morph_batch_launch() on the plan, and copies
+ * out_bytes from device memory d_out to host memory h_out, in that order on
+ * `stream` (one cudaMemcpyAsync per copy).  The caller lays the plan's
+ * source pages out in d_in and its destination pages in d_out; h_in and
+ * h_out should be page-locked (cudaHostAlloc) for the copies to be
+ * asynchronous.  Returns once the work is queued; morph_sync_status(stream)
+ * waits for it.  Two calls on two streams with two plans and buffer sets
+ * overlap one step's copies with the other's kernels.  Errors: MORPH_EINVAL
+ * (a NULL buffer with a nonzero size), those of morph_batch_launch(),
+ * MORPH_ECUDA. */
+MORPH_API morph_status morph_batch_launch_host(const void *dev_plan, const void *host_plan,
+                                               void *workspace, size_t workspace_bytes,
+                                               const void *h_in, void *d_in, size_t in_bytes,
+                                               void *h_out, const void *d_out, size_t out_bytes,
+                                               void *stream);
+
 /* ---------------------------------------------------------------- status -- */
 /* Wait for `stream`, then return (and clear) the first device-side condition
  * latched since the last call (MORPH_ECAPACITY, MORPH_ETIMEOUT), else the

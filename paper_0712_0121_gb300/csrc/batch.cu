@@ -1136,4 +1136,31 @@ morph_status morph_batch_launch(const void *dev_plan, const void *host_plan, voi
     return MORPH_OK;
 }
 
+morph_status morph_batch_launch_host(const void *dev_plan, const void *host_plan, void *workspace,
+                                     size_t workspace_bytes, const void *h_in, void *d_in, size_t in_bytes,
+                                     void *h_out, const void *d_out, size_t out_bytes, void *stream) {
+    if ((in_bytes && (!h_in || !d_in)) || (out_bytes && (!h_out || !d_out))) {
+        set_error("batch host launch: NULL buffer with a nonzero size");
+        return MORPH_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (in_bytes) {
+        const cudaError_t e = cudaMemcpyAsync(d_in, h_in, in_bytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            set_error("batch host launch: copy in: %s", cudaGetErrorString(e));
+            return MORPH_ECUDA;
+        }
+    }
+    const morph_status st = morph_batch_launch(dev_plan, host_plan, workspace, workspace_bytes, 0, stream);
+    if (st != MORPH_OK) return st;
+    if (out_bytes) {
+        const cudaError_t e = cudaMemcpyAsync(h_out, d_out, out_bytes, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) {
+            set_error("batch host launch: copy out: %s", cudaGetErrorString(e));
+            return MORPH_ECUDA;
+        }
+    }
+    return MORPH_OK;
+}
+
 }  // extern "C"

@@ -139,6 +139,8 @@ def _load():
     lib.morph_batch_plan_debug.restype = ci
     lib.morph_batch_launch.argtypes = [vp, vp, vp, sz, ci, vp]
     lib.morph_batch_launch.restype = ci
+    lib.morph_batch_launch_host.argtypes = [vp, vp, vp, sz, vp, vp, sz, vp, vp, sz, vp]
+    lib.morph_batch_launch_host.restype = ci
     lib.morph_rle_rect_noalloc.argtypes = [ci, img_p, img_p, ci, ci, ci, ci, vp]
     lib.morph_rle_rect_noalloc.restype = ci
     return lib
@@ -604,6 +606,19 @@ class Batch:
         _check(_lib.morph_batch_launch(self.dev_plan.data_ptr(), self.host_plan.ctypes.data,
                                        self.workspace.data_ptr(), self.ws_bytes, n_ctas,
                                        _stream_handle(stream)))
+
+    def launch_host(self, h_in: torch.Tensor, d_in: torch.Tensor, h_out: torch.Tensor, d_out: torch.Tensor,
+                    stream=None) -> None:
+        """``morph_batch_launch_host``: copy ``h_in`` (host, pinned) into
+        ``d_in``, launch, copy ``d_out`` into ``h_out`` (host, pinned), all on
+        ``stream``; the plan's pages live in ``d_in`` / ``d_out``."""
+        nin, nout = h_in.numel() * h_in.element_size(), h_out.numel() * h_out.element_size()
+        if d_in.numel() * d_in.element_size() < nin or d_out.numel() * d_out.element_size() < nout:
+            raise ValueError("device buffers smaller than the host buffers")
+        _check(_lib.morph_batch_launch_host(self.dev_plan.data_ptr(), self.host_plan.ctypes.data,
+                                            self.workspace.data_ptr(), self.ws_bytes, h_in.data_ptr(),
+                                            d_in.data_ptr(), nin, h_out.data_ptr(), d_out.data_ptr(), nout,
+                                            _stream_handle(stream)))
 
     def capture(self, n_ctas: int = 0) -> "torch.cuda.CUDAGraph":
         """Capture one launch in a CUDA graph (replay with ``g.replay()``)."""

@@ -222,3 +222,30 @@ def test_groups_only_launch_reuses_the_encodes():
     check_all(jobs, imgs)
     b.debug(2, 0)
     assert b.kernels == full
+
+
+def test_batch_between_host_buffers_on_two_calls():
+    """morph_batch_launch_host: the pages go in from pinned host memory, the
+    batch runs, the results come back to pinned host memory — all queued on
+    one stream; the second call with other pages in the same host buffer
+    gives that input's results."""
+    W, H, K = 700, 333, 3
+    ops = [("open", (7, 7), "packed"), ("close", (15, 15), "rle"), ("erode", (51, 1), "packed")]
+    d_in = torch.empty((K, H, (W + 63) // 64), dtype=torch.int64, device="cuda")
+    d_out = torch.empty((K, H, (W + 63) // 64), dtype=torch.int64, device="cuda")
+    jobs = [dict(op=op, se=se, path=path, src=M.Packed(d_in[k], W), dst=M.Packed(d_out[k], W))
+            for k, (op, se, path) in enumerate(ops)]
+    b = M.Batch(jobs)
+    h_in = torch.empty(d_in.shape, dtype=torch.int64, pin_memory=True)
+    h_out = torch.empty(d_out.shape, dtype=torch.int64, pin_memory=True)
+    for call in range(2):
+        imgs = [synth.text_page(W, H, 9500 + 10 * call + k, 0.15, glyph=(4, 12, 6, 14), gap=(2, 6))[0]
+                for k in range(K)]
+        for k, img in enumerate(imgs):
+            h_in[k].copy_(M.pack(img, 64).words.cpu())
+        h_out.fill_(-1)
+        b.launch_host(h_in, d_in, h_out, d_out)
+        assert M.sync_status() == M.MORPH_OK
+        for k, (img, (op, (sw, sh), _)) in enumerate(zip(imgs, ops)):
+            ref = oracle.apply(op, img, sw, sh, mode="separable", threads=NCORES)
+            assert np.array_equal(unpack_words(h_out[k], W), ref), (call, k, op)

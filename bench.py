@@ -437,8 +437,8 @@ def run_config1(M, stream, reps):
 
 def run_uneven_batch(M, args, stream):
     """Uneven batch: seeded pages of four sizes, ink density U(1,30) %, each
-    with its own rectangle and op; per-page path and band from the autotuner
-    (tuned per page size); one batch launch (CUDA graph) vs the same
+    with its own rectangle and op; per-page path, band and word tile from
+    the autotuner (tuned per page size); one batch launch (CUDA graph) vs the same
     per-page launches captured in one CUDA graph, and vs a host loop of
     them."""
     import torch
@@ -456,12 +456,17 @@ def run_uneven_batch(M, args, stream):
     t_tune = time.perf_counter() - t0
     imgs = pmap(lambda j: synth.config4_page(j)[0], specs)
     jobs, npix, nrle = [], 0, 0
+    wchosen = {}  # packed pages per size by the word tile the tuner chose
     for j, img in zip(specs, imgs):
         src = M.pack(img, 64)
         dst = M.Packed.empty(j["W"], j["H"], 64)
         path, band = tuner.choose(j["W"], j["H"], j["op"], j["se"], j["density"])
+        words = tuner.words(j["W"], j["H"], j["op"], j["se"])
         nrle += path == "rle"
-        jobs.append(dict(op=j["op"], se=j["se"], path=path, tile_rows=band, src=src, dst=dst))
+        if path == "packed":
+            wkey = "%dx%d" % (j["W"], j["H"])
+            wchosen.setdefault(wkey, {"planner": 0, "2": 0, "4": 0})[str(words) if words else "planner"] += 1
+        jobs.append(dict(op=j["op"], se=j["se"], path=path, tile_rows=band, words_per_thread=words, src=src, dst=dst))
         npix += j["W"] * j["H"]
     del imgs
     batch = M.Batch(jobs)
@@ -505,6 +510,7 @@ def run_uneven_batch(M, args, stream):
     alg = sum(2 * j["src"].height * ((j["src"].width + 63) // 64) * 8 for j in jobs)
     return {"pages": len(jobs), "rle_path_pages": nrle, "megapixels": round(npix / 1e6, 1),
             "size_classes_tuned": [list(sz) for sz in sizes],
+            "words_per_thread_chosen": wchosen,
             "batch_ms": round(tb, 3), "batch_pages_s": round(len(jobs) / tb * 1e3, 1),
             "batch_gpix_s": round(npix / tb / 1e6, 1),
             "batch_roofline": {"alg_bytes": int(alg), "alg_gb_s": round(alg / tb / 1e6, 1),

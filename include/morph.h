@@ -435,6 +435,10 @@ typedef struct morph_job {
     int32_t tile_rows;   /* packed path: row-band height of its tiles; RLE path
                             and MORPH_TO_RLE: rows per work item (0 = the
                             plan's tile_rows, else the library default) */
+    int32_t words_per_thread;  /* packed path: 32-bit words each thread of the
+                            rectangle tile covers, 2 or 4 (0 = the planner's
+                            choice; a tiling the tile cannot hold falls back
+                            to the persistent kernel); ignored elsewhere */
     morph_image src;     /* packed */
     morph_image dst;     /* packed, same size; RLE for MORPH_TO_RLE */
 } morph_job;

@@ -1,9 +1,12 @@
 """Autotuner for the batch launch: per page class it measures
 
-* the row-band height of packed tiles (``tile_rows``), and
+* the row-band height of packed tiles (``tile_rows``),
+* the packed tile's word tile (2 or 4 32-bit words per thread, or the
+  planner's own choice), and
 * packed path versus RLE path, over a grid of ink densities,
 
-and answers :func:`Tuner.choose` (path, tile_rows) for a page from its size,
+and answers :func:`Tuner.choose` (path, tile_rows) and :func:`Tuner.words`
+(words per thread) for a page from its size,
 operation, rectangle and ink density — the runtime algorithm selection the
 paper proposes between bit blit and run-length methods (section
 "Experiments", choosing by mask size or output complexity), measured on this
@@ -21,6 +24,7 @@ import statistics
 
 DENSITIES = (0.005, 0.02, 0.05, 0.1, 0.2, 0.3)
 BANDS = (32, 64, 128, 256, 512)
+WORDS = (2, 4)  # 32-bit words per thread of the packed tile, besides the planner's choice
 
 
 def _key(W, H, op, se):
@@ -105,9 +109,19 @@ class Tuner:
             if t < best_t:
                 best_band, best_t = band, t
         entry["band"] = best_band
+        # the word tile at that band: the planner's choice (0) unless 2 or 4
+        # words per thread measure faster
+        best_words = 0
+        for words in WORDS:
+            t = self._time_batch(jobs_of(mid, path="packed", tile_rows=best_band, words_per_thread=words),
+                                 self.reps)
+            if t < best_t:
+                best_words, best_t = words, t
+        entry["words"] = best_words
         for dens in densities:
             pg = pages[dens] if pages is not None else self._pages(W, H, dens, n)
-            tp = self._time_batch(jobs_of(pg, path="packed", tile_rows=best_band), self.reps)
+            tp = self._time_batch(jobs_of(pg, path="packed", tile_rows=best_band, words_per_thread=best_words),
+                                  self.reps)
             tr = self._time_batch(jobs_of(pg, path="rle"), self.reps)
             entry["density"].append(dens)
             entry["packed_ms"].append(tp / total)
@@ -126,6 +140,14 @@ class Tuner:
     def tuned(self, W, H) -> bool:
         """Whether any class of this page size has been measured."""
         return any(k.startswith("%dx%d:" % (W, H)) for k in self.table)
+
+    def words(self, W, H, op, se, ref_size=None) -> int:
+        """Words per thread of the packed tile for the class (0 = the
+        planner's choice, also for untuned classes and older caches)."""
+        if ref_size is not None:
+            W, H = ref_size
+        e = self.table.get(_key(W, H, op, se))
+        return int(e.get("words", 0)) if e else 0
 
     def choose(self, W, H, op, se, density, ref_size=None):
         """(path, tile_rows) for one page; ``ref_size`` maps the page to the

@@ -521,6 +521,8 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
         const morph_image &s = q.src, &d = q.dst;
         auto packed = [](const morph_image &m) { return m.fmt == MORPH_PACKED32 || m.fmt == MORPH_PACKED64; };
         if (q.tile_rows < 0) return berr(MORPH_EINVAL, "tile_rows must be >= 0", j);
+        if (q.words_per_thread != 0 && q.words_per_thread != 2 && q.words_per_thread != 4)
+            return berr(MORPH_EINVAL, "words_per_thread must be 0, 2 or 4", j);
         if (q.depends_on < -1 || q.depends_on >= j)
             return berr(MORPH_EINVAL, "depends_on must be -1 or an earlier job", j);
         b.dep = q.depends_on;
@@ -595,7 +597,7 @@ morph_status build(const morph_job *jobs, int n, int tile_rows, int rle_runs_per
             ra.H = H;
             ra.nw_valid = (W + 31) / 32;
             ra.nw_cover = nw_cover;
-            if (rect_plan(ra, q.op, c.sw, c.sh, c.ox, c.oy, band_hint, 0, 0, 0) == 0) {
+            if (rect_plan(ra, q.op, c.sw, c.sh, c.ox, c.oy, band_hint, 0, q.words_per_thread, 0) == 0) {
                 ra.band_auto = 0;
                 b.path = q.path;
                 b.nphase = 0;  // no work in the persistent kernel

@@ -61,6 +61,7 @@ class morph_job(ctypes.Structure):
         ("origin_y", ctypes.c_int32),
         ("depends_on", ctypes.c_int32),
         ("tile_rows", ctypes.c_int32),
+        ("words_per_thread", ctypes.c_int32),
         ("src", morph_image),
         ("dst", morph_image),
     ]
@@ -552,7 +553,8 @@ class Batch:
     ``origin`` ((ox, oy), default centre), ``path`` ("packed" or "rle"),
     ``src`` (:class:`Packed`), ``dst`` (:class:`Packed`, or :class:`Rle` for
     "to_rle"), optional ``depends_on`` (index of an earlier job) and
-    ``tile_rows`` (row-band height of packed tiles).
+    ``tile_rows`` (row-band height of packed tiles) and ``words_per_thread``
+    (2 or 4: the packed tile's word tile; 0 = the planner's choice).
     The plan is built on the host, copied to the device once, and every
     :meth:`launch` is one call of ``morph_batch_launch`` (:attr:`kernels`
     kernel launches: grouped tile launches and the persistent kernel;
@@ -572,6 +574,7 @@ class Batch:
             arr[k].op = TO_RLE if j["op"] == "to_rle" else OPS.get(j["op"], j["op"])
             arr[k].depends_on = j.get("depends_on", -1)
             arr[k].tile_rows = j.get("tile_rows", 0)
+            arr[k].words_per_thread = j.get("words_per_thread", 0)
             arr[k].path = PATH_RLE if path in ("rle", PATH_RLE) else PATH_PACKED
             arr[k].se_w, arr[k].se_h, arr[k].origin_x, arr[k].origin_y = sw, sh, ox, oy
             arr[k].src = j["src"].desc()

@@ -27,3 +27,13 @@ def test_cache_round_trip(tmp_path):
     t.table = table()
     t.save()
     assert Tuner(cache_path=p).table == table()
+
+
+def test_word_tile_of_a_class():
+    t = Tuner()
+    t.table = table()
+    assert t.words(100, 200, "open", (31, 31)) == 0          # older entries: the planner's choice
+    t.table[_key(100, 200, "open", (31, 31))]["words"] = 4
+    assert t.words(100, 200, "open", (31, 31)) == 4
+    assert t.words(7, 7, "open", (31, 31), ref_size=(100, 200)) == 4
+    assert t.words(100, 200, "close", (3, 3)) == 0            # untuned class

@@ -249,3 +249,28 @@ def test_batch_between_host_buffers_on_two_calls():
         for k, (img, (op, (sw, sh), _)) in enumerate(zip(imgs, ops)):
             ref = oracle.apply(op, img, sw, sh, mode="separable", threads=NCORES)
             assert np.array_equal(unpack_words(h_out[k], W), ref), (call, k, op)
+
+
+@pytest.mark.parametrize("words", [2, 4])
+def test_word_tile_per_job(words):
+    """A job's words_per_thread picks the packed tile's word tile; every
+    operation and window class stays bit-exact (a tiling the tile cannot
+    hold falls back to the persistent kernel, also exact)."""
+    specs = [(300, 200, "erode", (3, 3), "packed", 0.2), (517, 333, "open", (9, 9), "packed", 0.25),
+             (1000, 50, "close", (1, 41), "packed", 0.15), (77, 640, "dilate", (101, 1), "packed", 0.05),
+             (200, 120, "open", (31, 31), "packed", 0.3), (2550, 400, "close", (51, 51), "packed", 0.08),
+             (640, 480, "open", (15, 15), "packed", 0.12)]
+    jobs, imgs = make_jobs(specs)
+    for j in jobs:
+        j["words_per_thread"] = words
+    b = M.Batch(jobs)
+    b.launch()
+    assert M.sync_status() == M.MORPH_OK
+    check_all(jobs, imgs)
+
+
+def test_word_tile_out_of_range_is_rejected():
+    jobs, _ = make_jobs([(64, 64, "erode", (3, 3), "packed", 0.3)])
+    jobs[0]["words_per_thread"] = 3
+    with pytest.raises(M.MorphError):
+        M.Batch(jobs)

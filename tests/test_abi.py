@@ -80,6 +80,19 @@ def test_host_argument_checks(M):
     assert b"reserved" in M.lib().morph_last_error()
 
 
+def test_batch_host_launch_rejects_null_buffers(M):
+    """``morph_batch_launch_host`` checks its host and device buffers before
+    any CUDA call: a NULL buffer with a nonzero size is MORPH_EINVAL."""
+    L, E = M.lib(), M.MORPH_EINVAL
+    buf = ctypes.create_string_buffer(64)
+    p = ctypes.addressof(buf)
+    assert L.morph_batch_launch_host(None, None, None, 0, None, p, 16, None, None, 0, None) == E
+    assert b"NULL buffer" in L.morph_last_error()
+    assert L.morph_batch_launch_host(None, None, None, 0, p, None, 16, None, None, 0, None) == E
+    assert L.morph_batch_launch_host(None, None, None, 0, None, None, 0, None, p, 16, None) == E
+    assert L.morph_batch_launch_host(None, None, None, 0, None, None, 0, p, None, 16, None) == E
+
+
 def test_rle_checks_and_workspace(M):
     def rle(W=100, H=10, rp=0x1000, runs=0x2000, cap=100):
         d = M.morph_image()

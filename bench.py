@@ -265,11 +265,20 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
+# A device-side delay queued before every timed launch (about 0.5 ms at a
+# 2.07 GHz SM clock): the start event and the launch are enqueued while it
+# runs, so the host's time to enqueue them (binding, plan, launch call) falls
+# outside the event pair, which then brackets the device work alone.
+QUEUE_AHEAD_CYCLES = 1_000_000
+
+
 def time_launches(fn, steps, stream):
     import torch
     times = []
     for _ in range(steps):
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            torch.cuda._sleep(QUEUE_AHEAD_CYCLES)
         s.record(stream)
         fn()
         e.record(stream)
@@ -408,7 +417,8 @@ def run_density_sweep(M, peak, stream, reps, copies):
 def run_config1(M, stream, reps):
     """512 x 512 text page (packed u32 rows): erode / dilate by 3x3, 11x1 and
     1x11 on the packed and RLE paths, and the RLE round trip.  One page is
-    32 KB and stays in L2: these are single-launch latencies."""
+    32 KB and stays in L2: device times of single launches (a page this
+    small leaves most SMs idle)."""
     import torch
     from paper_0712_0121_gb300 import synth
     img, ink = synth.config1_page()

@@ -1,0 +1,84 @@
+"""Host-side helpers of bench.py, on the CPU: the clock record taken during
+the timed steps, and the DRAM traffic read from a committed ncu record that
+is tied to the dominant kernel's sources by a digest."""
+import os
+import sys
+import threading
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+class _Proc:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def _sampler(lines):
+    c = bench.ClockSampler(0)
+    c.proc = _Proc()
+    c._t = threading.Thread(target=lambda: None)
+    c._t.start()
+    c.lines = list(lines)
+    return c
+
+
+NOT = "Not Active"
+
+
+def test_clock_record_median_max_and_active_reasons():
+    lines = [
+        "0, 2070, 2070, 910.2, 0x0000000000000000, %s, %s, %s, %s" % (NOT, NOT, NOT, NOT),
+        "0, 1965, 2070, 1391.0, 0x0000000000000004, %s, %s, %s, Active" % (NOT, NOT, NOT),
+        "0, 2070, 2070, 1002.7, 0x0000000000000000, %s, %s, %s, %s" % (NOT, NOT, NOT, NOT),
+        "not a sample",
+        "0, [N/A], 2070, 1000, 0x0, %s, %s, %s, %s" % (NOT, NOT, NOT, NOT),
+    ]
+    r = _sampler(lines).stop()
+    assert r["samples"] == 3
+    assert r["sm_mhz"] == 2070.0 and r["sm_max_mhz"] == 2070.0
+    assert r["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_record_names_every_slowdown_seen():
+    lines = ["0, 1500, 2070, 700, 0x68, Active, %s, %s, %s" % (NOT, NOT, NOT),
+             "0, 1400, 2070, 700, 0x68, %s, Active, Active, %s" % (NOT, NOT)]
+    r = _sampler(lines).stop()
+    assert r["sm_mhz"] == 1450.0
+    assert r["reasons"] == ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"]
+
+
+def test_clock_record_without_nvidia_smi():
+    c = bench.ClockSampler(0)
+    assert c.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def _record(tmp_path, digest, pages=4, dram=1000):
+    os.makedirs(tmp_path / "profiles", exist_ok=True)
+    (tmp_path / "profiles" / "rec.md").write_text(
+        "# a kernel\n\n| kernel | note: with a colon |\n|---|---|\n\n"
+        "- pages: %d\n- dram_bytes_per_launch: %d\n- csrc_sha256: %s\n" % (pages, dram, digest))
+
+
+def test_traffic_record_is_scaled_to_the_pages_while_the_digest_matches(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "csrc_digest", lambda: "abc123")
+    _record(tmp_path, "abc123", pages=4, dram=1000)
+    assert bench.profile_traffic("rec.md", 10) == 2500
+    _record(tmp_path, "0ther", pages=4, dram=1000)           # taken from other sources
+    assert bench.profile_traffic("rec.md", 10) is None
+    assert bench.profile_traffic("missing.md", 10) is None
+    (tmp_path / "profiles" / "rec.md").write_text("- pages: 4\n- csrc_sha256: abc123\n")
+    assert bench.profile_traffic("rec.md", 10) is None      # no byte count
+
+
+def test_digest_covers_the_dominant_kernels_sources():
+    d = bench.csrc_digest()
+    assert len(d) == 64 and int(d, 16) >= 0
+    for f in bench.DOMINANT_SOURCES:
+        assert os.path.exists(os.path.join(ROOT, "paper_0712_0121_gb300", "csrc", f)), f

@@ -85,6 +85,8 @@ def _load():
             lib.oracle_run_length_hist.restype = None
             lib.oracle_transpose.argtypes = [u8p, u8p, ci, ci]
             lib.oracle_transpose.restype = None
+            lib.oracle_rle_transpose_sweep.argtypes = [i32p, u16p, ctypes.c_int64, i32p, u16p, ci, ci]
+            lib.oracle_rle_transpose_sweep.restype = ctypes.c_int64
             lib.oracle_sheared_line.argtypes = [u8p, u8p, ci, ci, i32p, ci, ci, ci]
             lib.oracle_sheared_line.restype = None
             lib.oracle_layout_gap.argtypes = [i64p, ci, ci]
@@ -411,6 +413,34 @@ def rle_transpose(row_ptr, runs, W: int, H: int):
     """Transpose of an RLE image (section "Efficient Transpose"):
     decode, transpose, encode; the result has width H and height W."""
     return rle_encode(transpose(rle_decode(row_ptr, runs, W, H)))
+
+
+def rle_transpose_sweep(row_ptr, runs, W: int, H: int):
+    """Transpose of an RLE image by the sweep of section "Efficient
+    Transpose" (a list of open column intervals with their start lines,
+    merged with each input line; see ``oracle_rle_transpose_sweep``), never
+    decoding a pixel: (row_ptr int32[W+1], runs uint16[N, 2]) of the H x W
+    result (width H, height W)."""
+    if H > 65535:
+        raise ValueError("the transpose's rows are H wide: H must be <= 65535 (16-bit run ends)")
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    rn = np.ascontiguousarray(runs, dtype=np.uint16).reshape(-1, 2)
+    if rp.shape != (H + 1,) or rp[0] != 0 or rp[-1] != rn.shape[0] or np.any(np.diff(rp) < 0):
+        raise ValueError("row_ptr is not a valid prefix array")
+    if rn.shape[0] == 0:
+        rn = np.zeros((1, 2), dtype=np.uint16)
+    out_rp = np.zeros(W + 1, dtype=np.int32)
+    # a column holds at most ceil(H / 2) separated runs
+    cap = W * ((H + 1) // 2)
+    out = np.zeros((max(cap, 1), 2), dtype=np.uint16)
+    n = int(_load().oracle_rle_transpose_sweep(_ptr(out_rp, ctypes.c_int32), _ptr(out, ctypes.c_uint16),
+                                               cap, _ptr(rp, ctypes.c_int32), _ptr(rn, ctypes.c_uint16),
+                                               W, H))
+    if n == -1:
+        raise ValueError("run list is not canonical")
+    if n < 0:
+        raise MemoryError("transpose sweep failed (%d)" % n)
+    return out_rp, out[:n].copy()
 
 
 # --------------------------------------------------- sheared line SEs ---

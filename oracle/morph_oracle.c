@@ -437,6 +437,110 @@ EXPORT void oracle_transpose(uint8_t *out, const uint8_t *in, int W, int H) {
         for (int x = 0; x < W; x++) out[(size_t)x * H + y] = in[(size_t)y * W + x];
 }
 
+/* The sweep of section "Efficient Transpose", for RLE images: instead of an
+ * open-run entry per output line, a list of open intervals of columns, each
+ * with the line its vertical runs started on.  Line y of the input is merged
+ * with the list in one left-to-right walk over the boundaries of both:
+ *   columns in an open interval and in a run of line y stay open (same start),
+ *   columns in an open interval but in no run close: each column x gets the
+ *     vertical run [start, y) in output line x,
+ *   columns in a run but in no open interval open with start y.
+ * After the last line every open interval closes at H.  Output line x
+ * receives its runs in the order they close, which is ascending, and two
+ * runs of a column are separated by at least the line that closed the first,
+ * so the output is canonical.
+ *
+ * Two walks over the image: the first counts each output line's runs into
+ * out_row_ptr (then turned into offsets), the second writes them.  Input:
+ * canonical runs (ascending, non-empty, separated, ends <= W; checked).
+ * Returns the number of output runs, -1 for a non-canonical input, -2 when
+ * the runs do not fit `cap`, -3 when out of host memory. */
+typedef struct { int a, b, s; } SweepIv;
+
+static void sweep_close(int x0, int x1, int start, int y, int32_t *cur, uint16_t *out_runs) {
+    for (int x = x0; x < x1; x++) {
+        if (out_runs) {
+            out_runs[2 * (int64_t)cur[x]] = (uint16_t)start;
+            out_runs[2 * (int64_t)cur[x] + 1] = (uint16_t)y;
+        }
+        cur[x]++;
+    }
+}
+
+static void sweep_open(SweepIv *nx, int *nn, int a, int b, int s) {
+    if (*nn > 0 && nx[*nn - 1].b == a && nx[*nn - 1].s == s) {
+        nx[*nn - 1].b = b;
+        return;
+    }
+    nx[*nn].a = a;
+    nx[*nn].b = b;
+    nx[*nn].s = s;
+    (*nn)++;
+}
+
+static int sweep_pass(const int32_t *row_ptr, const uint16_t *runs, int W, int H, int32_t *cur,
+                      uint16_t *out_runs, SweepIv *op, SweepIv *nx) {
+    int no = 0;
+    for (int y = 0; y < H; y++) {
+        const int64_t r0 = row_ptr[y], r1 = row_ptr[y + 1];
+        for (int64_t r = r0; r < r1; r++) {
+            const int s = runs[2 * r], e = runs[2 * r + 1];
+            if (s >= e || e > W || (r > r0 && s <= runs[2 * r - 1])) return -1;
+        }
+        int nn = 0, p = 0, x = 0;
+        int64_t q = r0;
+        while (p < no || q < r1) {
+            const int oa = p < no ? op[p].a : INT32_MAX, ob = p < no ? op[p].b : INT32_MAX;
+            const int ra = q < r1 ? runs[2 * q] : INT32_MAX, rb = q < r1 ? runs[2 * q + 1] : INT32_MAX;
+            if (x < oa && x < ra) x = oa < ra ? oa : ra;
+            const int in_o = oa <= x && x < ob, in_r = ra <= x && x < rb;
+            int z = INT32_MAX;
+            if (in_o) { if (ob < z) z = ob; } else if (oa < z) z = oa;
+            if (in_r) { if (rb < z) z = rb; } else if (ra < z) z = ra;
+            if (in_o && in_r) sweep_open(nx, &nn, x, z, op[p].s);
+            else if (in_o) sweep_close(x, z, op[p].s, y, cur, out_runs);
+            else sweep_open(nx, &nn, x, z, y);
+            x = z;
+            if (p < no && op[p].b <= x) p++;
+            if (q < r1 && runs[2 * q + 1] <= x) q++;
+        }
+        SweepIv *t = op;
+        op = nx;
+        nx = t;
+        no = nn;
+    }
+    for (int p = 0; p < no; p++) sweep_close(op[p].a, op[p].b, op[p].s, H, cur, out_runs);
+    return 0;
+}
+
+EXPORT int64_t oracle_rle_transpose_sweep(int32_t *out_row_ptr, uint16_t *out_runs, int64_t cap,
+                                          const int32_t *row_ptr, const uint16_t *runs, int W,
+                                          int H) {
+    /* an interval list never holds more entries than W (they are disjoint,
+     * non-empty column ranges) */
+    SweepIv *a = (SweepIv *)malloc(sizeof(SweepIv) * (size_t)(W + 1));
+    SweepIv *b = (SweepIv *)malloc(sizeof(SweepIv) * (size_t)(W + 1));
+    int32_t *cnt = (int32_t *)calloc((size_t)W + 1, sizeof(int32_t));
+    int64_t total = -3;
+    if (!a || !b || !cnt) goto done;
+    total = -1;
+    if (sweep_pass(row_ptr, runs, W, H, cnt, NULL, a, b)) goto done;
+    out_row_ptr[0] = 0;
+    for (int x = 0; x < W; x++) out_row_ptr[x + 1] = out_row_ptr[x] + cnt[x];
+    total = out_row_ptr[W];
+    if (total > cap) {
+        total = -2;
+        goto done;
+    }
+    for (int x = 0; x < W; x++) cnt[x] = out_row_ptr[x];
+    sweep_pass(row_ptr, runs, W, H, cnt, out_runs, a, b);
+done:
+    free(a);
+    free(b);
+    free(cnt);
+    return total;
+}
+
 /* --------------------------------------------------- sheared line SEs */
 
 /* Section "Morphology with Lines at Arbitrary Orientations": a line at an
